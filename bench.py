@@ -1,0 +1,352 @@
+"""Benchmark of the separable width-5 convolution on GB300.
+
+One step = one pass of the product path over one synthetic image: the fused
+single-pass kernel on a 3 x 8192 x 8192 FP32 image (k = five seeded uniform
+values normalised to sum 1), input and output resident in HBM.  The image
+(805 MB in, 804 MB out) is far larger than the 129 MB L2, so no flush is
+needed between steps.  Beside it, in the same run: the two-pass kernel pair
+on the same image, the end-to-end offload call with host buffers
+(sepconv5_run_host), the empty-launch overhead probe, and the FP64 CPU
+oracle timed on a bounded sample (rank 0, one GPU only).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (launched by torchrun): every rank convolves its own image (no
+collective on the data path; weak scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P, H, W = 3, 8192, 8192
+SEED = 2
+WORKLOAD = "3x8192x8192 f32 fused single-pass, k = 5 seeded uniform(0,1) taps / sum"
+METRIC = "3-plane Mpix/s (fused single-pass, 3x8192x8192 FP32)"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_f32_3x8192x8192.md")
+FUSED_SOURCES = ["sc5_fused_impl.cuh", "sc5_device.cuh", "sc5_fused_f32.cu", "sc5_fused.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip two-pass / e2e / probe / cpu legs")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def algorithmic_bytes(h: int, w: int, planes: int = P, es_in: int = 4, es_out: int = 4) -> int:
+    """One read of every input pixel and one write of every VALID output pixel."""
+    return planes * h * w * es_in + planes * (h - 4) * (w - 4) * es_out
+
+
+def measured_peaks() -> dict | None:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return None
+
+
+def fused_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in FUSED_SOURCES:
+        with open(os.path.join(ROOT, "paper_1711_09791_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic() -> int | None:
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != fused_source_hash():
+        return None
+    return int(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        # median under load: samples at the top half of the observed clocks
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+
+def oracle_sample(A: np.ndarray, k: np.ndarray, target_s: float = 10.0) -> dict:
+    """Time the FP64 oracle (single thread, as it stands) on the top band of
+    the image, sized to about target_s seconds; returns 3-plane Mpix/s."""
+    import oracle
+    k64 = k.astype(np.float64)
+    # calibrate on a small band
+    t0 = time.perf_counter()
+    oracle.direct(A[:, :36, :].astype(np.float64), k64)
+    per_row = (time.perf_counter() - t0) / 32.0
+    rows = int(max(32, min(H - 4, target_s / max(per_row, 1e-9))))
+    band = A[:, :rows + 4, :]
+    t0 = time.perf_counter()
+    oracle.direct(band.astype(np.float64), k64)
+    dt = time.perf_counter() - t0
+    px = rows * (W - 4)
+    return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"top {rows + 4} input rows x {W} cols x {P} planes of the image ({rows} x {W - 4} "
+                      f"output pixels), FP64 direct Eq. 1, one thread, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ main legs
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_1711_09791_gb300 import sepconv5, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sepconv5.load()
+    A = synth.image(SEED + rank, H, W)
+    k = synth.kernel_normalised(SEED)
+    A_dev = torch.from_numpy(A).to(dev)
+    out = torch.empty((P, H - 4, W - 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = sepconv5.Plan(P, H, W, W, W - 4, algo="fused")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        n0 = sepconv5.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        return max_over_ranks(ms), sepconv5.launch_count() - n0
+
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    smi_index = vis[local_rank] if local_rank < len(vis) and vis[local_rank].isdigit() else str(local_rank)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    ms, launches = timed(lambda: plan.run(A_dev, out, k, stream=stream), args.steps, max(args.warmup, 3))
+    clocks = sampler.stop()
+    if sepconv5.device_status(stream) != 0:
+        raise RuntimeError("a kernel reported a device error during the timed region")
+
+    alg = algorithmic_bytes(H, W)
+    pixels = H * W
+    value = world * pixels / (ms / 1e3) / 1e6
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = alg / (ms / 1e3) / 1e9
+    extras = {}
+    if not args.no_extras:
+        # two-pass pair on the same image, same algorithmic bytes
+        plan2 = sepconv5.Plan(P, H, W, W, W - 4, algo="two_pass")
+        k2 = max(20, args.steps // 4)
+        ms2, l2 = timed(lambda: plan2.run(A_dev, out, k, stream=stream), k2, 5)
+        plan2.close()
+        extras["two_pass"] = {"ms_per_step": round(ms2, 5), "value": round(world * pixels / (ms2 / 1e3) / 1e6, 1),
+                              "unit": "Mpix/s", "achieved_gbs": round(alg / (ms2 / 1e3) / 1e9, 1),
+                              "frac_of_measured_hbm": round(alg / (ms2 / 1e3) / 1e9 / peak, 4),
+                              "launches_per_step": l2 / k2, "fused_speedup": round(ms2 / ms, 3)}
+        # empty-kernel launch overhead
+        n_probe = 2000
+        ms_probe, _ = timed(lambda: sepconv5.empty_launches(1, stream), n_probe, 50)
+        extras["empty_launch_us"] = round(ms_probe * 1e3, 3)
+    # end to end: host buffers through sepconv5_run_host
+    A_host = torch.from_numpy(A).pin_memory()
+    out_host = torch.empty((P, H - 4, W - 4), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps // 50, 20))
+    for _ in range(2):
+        plan.run_host(A_host, out_host, k, stream=stream)
+    barrier()
+    n0 = sepconv5.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.run_host(A_host, out_host, k, stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps)
+    e2e_launches = (sepconv5.launch_count() - n0) / e2e_steps
+    # spot check the e2e result against the device result
+    if not torch.equal(out_host[:, ::1024, ::1024].to(dev), out[:, ::1024, ::1024]):
+        raise RuntimeError("offload result differs from the device result")
+    e2e = {"value": round(world * pixels / (e2e_ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
+           "h2d_bytes_per_step": P * H * W * 4, "d2h_bytes_per_step": P * (H - 4) * (W - 4) * 4,
+           "ms_per_step": round(e2e_ms, 4), "launches_per_step": e2e_launches,
+           "api": "sepconv5_run_host (pinned host buffers, band-pipelined copies)"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        cpu = oracle_sample(A, k)
+    plan.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid",
+                   "l2": "inputs larger than L2 (805 MB in, 804 MB out per step); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                     "peak_source": peak_src, "kernel": "fused_kernel<float,float> (single image)",
+                     "algorithmic_bytes_per_launch": alg},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    return line
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle, as it stands, on the host cores: each step a bounded sample
+    (a band of rows) of the same image and kernel."""
+    if rank != 0:
+        return None
+    from paper_1711_09791_gb300 import synth
+    import oracle
+    A = synth.image(SEED, H, W)
+    k = synth.kernel_normalised(SEED).astype(np.float64)
+    rows = 512  # output rows per step: a fraction of a second of single-threaded FP64 work
+    band = A[:, :rows + 4, :].astype(np.float64)
+    for _ in range(3):
+        oracle.direct(band, k)
+    steps = max(1, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.direct(band, k)
+    dt = (time.perf_counter() - t0) / steps
+    value = rows * (W - 4) / dt / 1e6
+    sample = f"{rows + 4} input rows x {W} cols x {P} planes per step ({rows} x {W - 4} output pixels), FP64 direct Eq. 1, one thread"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world,
+            "steps": steps, "warmup": 3, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,282 @@
+/*
+ * sepconv5.h -- C ABI of libsepconv5, a GB300 (sm_103a) library for the
+ * convolution of planar multi-plane images by a separable width-5 kernel
+ * (arXiv 1711.09791, "2D Image Convolution using Three Parallel Programming
+ * Models on the Xeon Phi").
+ *
+ * The operation (Eq. 1 of Sec. 1, with the separable matrix K[i][j] = k[i]k[j]):
+ *
+ *     B[p][y][x] = sum_{a=0..4} sum_{b=0..4} A[p][y+a-2][x+b-2] * k[a] * k[b]
+ *
+ * evaluated for every plane p and every interior pixel (y, x) with
+ * 2 <= y < H-2 and 2 <= x < W-2.  The paper ignores the image edges and starts
+ * the convolution at pixel (2,2) (Sec. 5, first paragraph); tap t of k acts at
+ * offset t-2 on both axes, with k[0] on the left/top neighbour (Eq. 2 and
+ * Listing 1).  It is a correlation: the kernel is not flipped.  Any 5 finite
+ * taps are accepted (they need not be symmetric or sum to 1).
+ *
+ * Two algorithms compute it (Sec. 5.1):
+ *   SC5_ALGO_FUSED     single pass: one kernel reads each input pixel from HBM
+ *                      once and writes each output pixel once; the horizontal
+ *                      pass result stays on chip (the "single-pass without
+ *                      copy-back" of Sec. 7, computed as the separable 5+5 form).
+ *   SC5_ALGO_TWO_PASS  the horizontal 1D pass writes an FP32 intermediate T to
+ *                      HBM, then the vertical 1D pass reads it (Sec. 5.1,
+ *                      Listing 1; the horizontal pass covers all H rows so
+ *                      that every output row is defined).
+ * Both accumulate in FP32 with the taps applied in the order t = 0..4 and give
+ * bitwise identical results.
+ *
+ * Conventions for every call:
+ *   - Status codes only; nothing throws across this boundary.  On failure,
+ *     sepconv5_last_error() returns a message for the calling thread.
+ *   - "dev" pointers are CUDA device pointers of the current device, "host"
+ *     pointers are CPU memory.  The caller owns every buffer it passes; a plan
+ *     or batch owns only the workspace it allocates itself.
+ *   - Image layout is planar: element (p, y, x) of an image with row pitch
+ *     `pitch` (in elements) and H rows sits at offset (p*H + y)*pitch + x.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Runs are asynchronous on that stream.
+ *   - Sizes: planes >= 1, H >= 5, W >= 5.  For the TMA loads the input base
+ *     address must be 16-byte aligned and in_pitch * element size a multiple
+ *     of 16 bytes; otherwise SC5_EINVAL.
+ *   - Thread safety: distinct plans/batches/servers may be used from
+ *     different threads; one plan must not be used by two threads at once.
+ */
+#ifndef SEPCONV5_H
+#define SEPCONV5_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+/* Exported symbols keep default visibility when the library is built with
+ * -fvisibility=hidden. */
+#if defined(__GNUC__)
+#define SC5_API __attribute__((visibility("default")))
+#else
+#define SC5_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SC5_OK = 0,
+    SC5_EINVAL = 1,     /* bad argument: sizes, alignment, null pointer, dtype/algo not built */
+    SC5_ENOMEM = 2,     /* device or host allocation failed */
+    SC5_ECUDA = 3,      /* a CUDA runtime/driver call failed */
+    SC5_EAGAIN = 4,     /* serve_submit: over budget or queue full; serve_poll: not done yet */
+    SC5_ETIMEDOUT = 5,  /* serve_poll: timeout expired before completion */
+    SC5_ENOTFOUND = 6,  /* unknown ticket / no tuning entry */
+    SC5_EDEVICE = 7     /* a kernel reported a device-side error (a bounded wait ran out) */
+} sc5_status;
+
+/* Storage formats.  A stored code c represents the real value value(c)/scale;
+ * the scale is a per-image float (1 for F32/BF16/F16 unless the caller says
+ * otherwise; for FP8 E4M3 typically 448/max|A|).  Arithmetic is always FP32. */
+typedef enum {
+    SC5_F32 = 0,        /* IEEE binary32 */
+    SC5_BF16 = 1,       /* bfloat16 */
+    SC5_F16 = 2,        /* IEEE binary16 */
+    SC5_FP8E4M3 = 3     /* OCP FP8 E4M3 (no infinities, max 448); stores saturate */
+} sc5_dtype;
+
+typedef enum {
+    SC5_BORDER_VALID = 0, /* out is [planes][H-4][out_pitch]; input pixel (2,2) -> out (0,0) */
+    SC5_BORDER_KEEP = 1   /* out is [planes][H][out_pitch]; interior as above, the 2-pixel
+                             frame is the input converted to the output format (the image
+                             Listing 1 leaves behind, computed out of place) */
+} sc5_border;
+
+typedef enum {
+    SC5_ALGO_FUSED = 0,
+    SC5_ALGO_TWO_PASS = 1
+} sc5_algo;
+
+/* Plan descriptor.  Pitches are in elements of the respective dtype.
+ * tile_h/tile_w/stages: 0 = take the autotuned (or built-in default) choice;
+ * otherwise one of the compiled fused-kernel shapes (sepconv5_fused_configs). */
+typedef struct {
+    int32_t planes, H, W;
+    int64_t in_pitch, out_pitch;
+    int32_t in_dtype, out_dtype;   /* sc5_dtype */
+    int32_t border;                /* sc5_border */
+    int32_t algo;                  /* sc5_algo */
+    int32_t tile_h, tile_w, stages;
+    int32_t ctas_per_sm;           /* 0 = as many as fit */
+} sc5_plan_desc;
+
+typedef struct sc5_plan_s *sc5_plan;
+
+/* One image of a batch or one serving request.
+ *   in, out: dev pointers for sepconv5_run_batch / sepconv5_batch_create;
+ *            host pointers for serve_submit.
+ *   H, W, pitches: as in sc5_plan_desc; planes and dtypes come from the plan
+ *   (batch) or the server configuration (serve).
+ *   k: the 5 taps; in_scale/out_scale: as for sepconv5_run. */
+typedef struct {
+    const void *in;
+    void *out;
+    int32_t H, W;
+    int64_t in_pitch, out_pitch;
+    float k[5];
+    float in_scale, out_scale;
+} sc5_image;
+
+/* ---------------------------------------------------------------- plans */
+
+/* Validate a descriptor and build a plan for one image shape.  Owns the
+ * workspace: the FP32 intermediate T of the two-pass form
+ * (planes*H*round_up(W-4,4)*4 bytes, allocated here) and a device status word.
+ * Returns SC5_EINVAL for bad sizes/pitches/dtypes, SC5_ENOMEM if the
+ * workspace cannot be allocated.  Calls cudaMalloc on the current device. */
+SC5_API sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out);
+SC5_API sc5_status sepconv5_plan_destroy(sc5_plan plan);
+
+/* Run the plan on one image: in (dev, in_dtype, [planes][H][in_pitch]),
+ * out (dev, out_dtype, layout per border), k (host, 5 taps, copied by
+ * value).  in_scale > 0 and out_scale > 0 must be finite; the result code is
+ * round(B * out_scale) with B computed from value(in)/in_scale.  `in` and
+ * `out` must not overlap.  Asynchronous on `stream`. */
+SC5_API sc5_status sepconv5_run(sc5_plan plan, const void *in, void *out, const float k[5],
+                        float in_scale, float out_scale, void *stream);
+
+/* Offload form (the co-processor model of Sec. 7: copy the image to the
+ * device, convolve, copy the result back): host_in and host_out are HOST
+ * pointers laid out as for sepconv5_run (pinned memory gives full copy
+ * bandwidth; pageable memory works but the copies are staged by the driver).
+ * The image is cut into bands of rows; the copy of band b+1 to the device,
+ * the kernel of band b and the copy of band b-1 back overlap on three
+ * streams.  Device staging buffers (input and output image) are allocated by
+ * the plan on first use and kept until it is destroyed.  Returns when the
+ * result is in host_out.  Fused form only; `stream` carries the kernels. */
+SC5_API sc5_status sepconv5_run_host(sc5_plan plan, const void *host_in, void *host_out, const float k[5],
+                                     float in_scale, float out_scale, void *stream);
+
+/* Two-pass form, one pass at a time (for checking each pass on its own).
+ * hpass writes T (dev, FP32, [planes][H][t_pitch]; t_pitch >= W-4 and a
+ * multiple of 4; T 16-byte aligned): column x of row y is the horizontal
+ * pass sum_t k[t] * value(in[y][x+t]) centred on input column x+2, for all H
+ * rows, on the stored values (not divided by in_scale).  vpass reads such a
+ * T and writes `out` exactly as sepconv5_run would. */
+SC5_API sc5_status sepconv5_hpass(sc5_plan plan, const void *in, float *T, int64_t t_pitch,
+                          const float k[5], void *stream);
+SC5_API sc5_status sepconv5_vpass(sc5_plan plan, const float *T, int64_t t_pitch, void *out,
+                          const float k[5], float in_scale, float out_scale, void *stream);
+
+/* Synchronise `stream`, then read and clear the device status word shared by
+ * every kernel of this library on the current device: 0 if no kernel
+ * reported an error since the last call, else SC5_EDEVICE with *code set to
+ * the kernel's error code (1 = an mbarrier wait for a TMA load ran out of
+ * time). */
+SC5_API sc5_status sepconv5_device_status(void *stream, int32_t *code);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Run many images of different sizes and kernels in one persistent launch
+ * driven by a tile work-list.  The plan supplies planes, dtypes, border and
+ * algo (must be SC5_ALGO_FUSED); its H/W are ignored.  imgs is a host array of
+ * n images whose in/out are dev pointers.  Builds the work-list and the
+ * per-image TMA descriptors on the host, uploads them to workspace owned by
+ * the plan (grown as needed, stream-ordered) and launches.  The tile shape is
+ * taken from the plan's override or from the autotuner for the batch's
+ * dominant size class. */
+SC5_API sc5_status sepconv5_run_batch(sc5_plan plan, int32_t n, const sc5_image *imgs, void *stream);
+
+/* A prepared batch: work-list and descriptors uploaded once, the launch
+ * captured in a CUDA graph.  sepconv5_batch_launch replays it on `stream`
+ * (the images' buffers must stay valid and keep their addresses). */
+typedef struct sc5_batch_s *sc5_batch;
+SC5_API sc5_status sepconv5_batch_create(sc5_plan plan, int32_t n, const sc5_image *imgs,
+                                 sc5_batch *out);
+SC5_API sc5_status sepconv5_batch_launch(sc5_batch batch, void *stream);
+/* Number of tiles and of CTAs of the prepared launch (for reporting). */
+SC5_API sc5_status sepconv5_batch_info(sc5_batch batch, int64_t *tiles, int32_t *ctas,
+                               int32_t *tile_h, int32_t *tile_w);
+SC5_API sc5_status sepconv5_batch_destroy(sc5_batch batch);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Compiled fused-kernel shapes for an (in, out) dtype pair: writes up to
+ * `cap` triples (tile_h, tile_w, stages) into cfg and their count to *n. */
+SC5_API sc5_status sepconv5_fused_configs(int32_t in_dtype, int32_t out_dtype, int32_t *cfg,
+                                  int32_t cap, int32_t *n);
+
+/* Autotuner (the counterpart of the paper's thread/task-count tuning, Sec. 4
+ * and Sec. 7): for every size class (log2 of the plane area, 6 classes from
+ * 2^12 to 2^26 pixels) and dtype pair in `dtypes` (pairs in, out), time every
+ * compiled shape and CTA count on synthetic images on the current device and
+ * keep the fastest.  mode: 0 = off (built-in defaults), 1 = quick (one size
+ * per class), 2 = full.  The table is kept in the process and, if path is
+ * not NULL, written there as JSON keyed by GPU name.  Allocates device memory
+ * for its test images. */
+SC5_API sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int32_t n_pairs,
+                             const char *path);
+/* Load a table written by sepconv5_autotune (entries for other GPUs are ignored). */
+SC5_API sc5_status sepconv5_tune_load(const char *path);
+/* The shape the planner would pick for a plane of H x W with these dtypes. */
+SC5_API sc5_status sepconv5_tune_lookup(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
+                                int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                int32_t *ctas_per_sm);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct sc5_server_s *sc5_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device bytes for resident request buffers */
+    int32_t max_inflight;     /* requests admitted and not yet completed */
+    int32_t dtype;            /* storage format of inputs and outputs */
+    int32_t planes;           /* planes per image */
+    int32_t n_streams;        /* compute streams used round robin (>= 1) */
+    int32_t max_merge;        /* most requests merged into one launch (0 = no limit) */
+    int32_t merge;            /* 1 = continuous batching, 0 = one launch per request */
+} sc5_serve_cfg;
+
+typedef struct {
+    uint64_t submitted, completed, launches, rejected;
+    uint64_t merged_max;         /* largest number of requests in one launch */
+    size_t resident_peak_bytes;  /* high-water mark of admitted buffers */
+} sc5_serve_stats;
+
+/* Start a server on the current device: allocates its resident arena
+ * (hbm_budget_bytes) and starts its scheduler and completion threads. */
+SC5_API sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out);
+
+/* Queue one request.  req->in and req->out are HOST pointers to
+ * [planes][H][pitch] images of the server's dtype; the server reads `in`
+ * and writes `out` asynchronously, so both must stay valid until serve_poll
+ * returns SC5_OK for the ticket (pinned memory gives the fastest copies).
+ * Returns SC5_EAGAIN when the request could never fit the budget together
+ * with what is queued (backpressure: retry later), SC5_EINVAL for bad shapes. */
+SC5_API sc5_status serve_submit(sc5_server srv, const sc5_image *req, uint64_t *ticket);
+
+/* Wait up to timeout_us (0 = just test, <0 = forever) for a ticket.  SC5_OK:
+ * the output is in req->out and *latency_us (if not NULL) holds the time from
+ * submit to completion of the device-to-host copy; the ticket is retired.
+ * SC5_EAGAIN (timeout_us == 0) or SC5_ETIMEDOUT: not done yet. */
+SC5_API sc5_status serve_poll(sc5_server srv, uint64_t ticket, int32_t timeout_us, double *latency_us);
+
+SC5_API sc5_status serve_get_stats(sc5_server srv, sc5_serve_stats *stats);
+
+/* Drain every queued and in-flight request, stop the threads, free the arena. */
+SC5_API sc5_status serve_destroy(sc5_server srv);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message for the last failing call on this thread ("" if none). */
+SC5_API const char *sepconv5_last_error(void);
+
+/* Launch an empty kernel `n` times on `stream` (the launch-overhead probe, the
+ * counterpart of the paper's empty-kernel measurement in Sec. 6). */
+SC5_API sc5_status sepconv5_empty_launches(int32_t n, void *stream);
+
+/* Number of kernels this library launched in this process (all entry points). */
+SC5_API int64_t sepconv5_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEPCONV5_H */

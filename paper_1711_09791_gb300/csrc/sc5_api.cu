@@ -1,0 +1,754 @@
+// sc5_api.cu -- the C ABI of libsepconv5: plans (validation, TMA tensor
+// maps, tile grid), single-image runs of both forms, batches with a tile
+// work-list (one-shot or captured in a CUDA graph), the device status word,
+// the empty-launch probe and the launch counter.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sc5_internal.h"
+#include "sc5_tune.h"
+
+namespace sc5 {
+
+static thread_local std::string t_err;
+static std::atomic<int64_t> g_launches{0};
+
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+sc5_status fail(sc5_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return st;
+}
+
+sc5_status fail_cuda(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SC5_ENOMEM : SC5_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { t_err.clear(); }
+
+int dtype_bytes(int dtype)
+{
+    switch (dtype) {
+    case SC5_F32: return 4;
+    case SC5_BF16:
+    case SC5_F16: return 2;
+    case SC5_FP8E4M3: return 1;
+    default: return 0;
+    }
+}
+
+int num_sms()
+{
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev];
+}
+
+static bool pair_supported(int in_dtype, int out_dtype)
+{
+    return fused_num_shapes(in_dtype, out_dtype) > 0;
+}
+
+// ------------------------------------------------------------------ tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map of a planar image (x = column, y = row, z = plane), box of
+// box_w x box_h x 1 elements, zero fill outside the image.
+static sc5_status encode_image_map(CUtensorMap *m, int dtype, const void *base, int P, int H, int W,
+                                   int64_t pitch, int box_w, int box_h)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(SC5_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int es = dtype_bytes(dtype);
+    CUtensorMapDataType t = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                            : es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                      : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H),
+                                static_cast<cuuint64_t>(P)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(pitch) * es,
+                                   static_cast<cuuint64_t>(pitch) * es * static_cast<cuuint64_t>(H)};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, t, 3, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SC5_EINVAL, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return SC5_OK;
+}
+
+static int box_w_for(int dtype, int tile_w)
+{
+    const int es = dtype_bytes(dtype);
+    return ((tile_w + kHalo) * es + 15) / 16 * 16 / es;
+}
+
+// ------------------------------------------------------------------ validation
+
+static sc5_status check_image(int in_dtype, int out_dtype, int border, const void *in, const void *out,
+                              int P, int H, int W, int64_t in_pitch, int64_t out_pitch, float in_scale,
+                              float out_scale, bool need_ptrs)
+{
+    if (P < 1 || H < 5 || W < 5) return fail(SC5_EINVAL, "need planes >= 1, H >= 5, W >= 5 (got %d, %d, %d)", P, H, W);
+    if (H > 65535 * 8 || W > (1 << 30)) return fail(SC5_EINVAL, "image too large (H <= 524280, W < 2^30)");
+    const int ei = dtype_bytes(in_dtype), eo = dtype_bytes(out_dtype);
+    if (!ei || !eo) return fail(SC5_EINVAL, "unknown dtype (%d, %d)", in_dtype, out_dtype);
+    if (border != SC5_BORDER_VALID && border != SC5_BORDER_KEEP) return fail(SC5_EINVAL, "unknown border %d", border);
+    const int64_t wout = border == SC5_BORDER_KEEP ? W : W - kHalo;
+    if (in_pitch < W) return fail(SC5_EINVAL, "in_pitch %lld < W %d", (long long)in_pitch, W);
+    if (out_pitch < wout) return fail(SC5_EINVAL, "out_pitch %lld < output width %lld", (long long)out_pitch, (long long)wout);
+    if ((in_pitch * ei) % 16) return fail(SC5_EINVAL, "in_pitch * element size must be a multiple of 16 bytes");
+    if ((static_cast<double>(in_pitch) * ei * H * P) >= 1099511627776.0) return fail(SC5_EINVAL, "image larger than 2^40 bytes");
+    if (!(in_scale > 0.f) || !std::isfinite(in_scale) || !(out_scale > 0.f) || !std::isfinite(out_scale))
+        return fail(SC5_EINVAL, "scales must be finite and > 0");
+    if (need_ptrs) {
+        if (!in || !out) return fail(SC5_EINVAL, "null image pointer");
+        if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
+        if (reinterpret_cast<uintptr_t>(out) % eo) return fail(SC5_EINVAL, "output not aligned to its element size");
+        const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+        const char *a_end = a + static_cast<size_t>(P) * H * in_pitch * ei;
+        const int64_t hout = border == SC5_BORDER_KEEP ? H : H - kHalo;
+        const char *b_end = b + static_cast<size_t>(P) * hout * out_pitch * eo;
+        if (a < b_end && b < a_end) return fail(SC5_EINVAL, "input and output overlap");
+    }
+    return SC5_OK;
+}
+
+static bool taps_finite(const float *k)
+{
+    for (int i = 0; i < kTaps; ++i)
+        if (!std::isfinite(k[i])) return false;
+    return true;
+}
+
+// Fill an ImgDesc for one image (tensor map included).
+static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border, const FusedShape &sh,
+                            const void *in, void *out, int P, int H, int W, int64_t in_pitch,
+                            int64_t out_pitch, const float *k, float in_scale, float out_scale)
+{
+    std::memset(d, 0, sizeof *d);
+    sc5_status st = encode_image_map(&d->tmap, in_dtype, in, P, H, W, in_pitch,
+                                     box_w_for(in_dtype, sh.tile_w), sh.tile_h + kHalo);
+    if (st != SC5_OK) return st;
+    const int eo = dtype_bytes(out_dtype);
+    char *ob = static_cast<char *>(out);
+    int64_t plane_rows = H - kHalo;
+    if (border == SC5_BORDER_KEEP) {
+        ob += (2 * out_pitch + 2) * eo;
+        plane_rows = H;
+    }
+    d->out = ob;
+    d->out_pitch = out_pitch;
+    d->out_plane = plane_rows * out_pitch;
+    d->Hv = H - kHalo;
+    d->Wv = W - kHalo;
+    d->tiles_x = (d->Wv + sh.tile_w - 1) / sh.tile_w;
+    d->tiles_y = (d->Hv + sh.tile_h - 1) / sh.tile_h;
+    for (int i = 0; i < kTaps; ++i) d->k[i] = k[i];
+    d->oscale = static_cast<float>(static_cast<double>(out_scale) / static_cast<double>(in_scale));
+    d->vec = (reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && out_pitch % 4 == 0) ? 1 : 0;
+    return SC5_OK;
+}
+
+}  // namespace sc5
+
+using namespace sc5;
+
+// ------------------------------------------------------------------ plans
+
+struct sc5_plan_s {
+    sc5_plan_desc d;
+    int device = 0;
+    int shape_idx = 0;
+    FusedShape shape{};
+    int ctas_per_sm = 1;
+    float *T = nullptr;
+    int64_t t_pitch = 0;
+    // batch workspace (device + pinned staging), grown on demand
+    unsigned char *ws_dev = nullptr;
+    size_t ws_cap = 0;
+    unsigned char *ws_host = nullptr;
+    size_t ws_host_cap = 0;
+    cudaEvent_t ws_done = nullptr;
+    bool ws_pending = false;
+    // offload staging (sepconv5_run_host)
+    void *stage_in = nullptr;
+    void *stage_out = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev;
+};
+
+static sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov,
+                               int *idx, int *ctas)
+{
+    if (ov && (ov->tile_h || ov->tile_w || ov->stages)) {
+        const int i = fused_find_shape(in_dtype, out_dtype, ov->tile_h ? ov->tile_h : 64,
+                                       ov->tile_w ? ov->tile_w : 128, ov->stages);
+        if (i < 0) return fail(SC5_EINVAL, "no compiled fused shape %dx%d with %d stages for this dtype pair",
+                               ov->tile_h, ov->tile_w, ov->stages);
+        *idx = i;
+        *ctas = ov->ctas_per_sm;
+    } else {
+        int th, tw, stg, c;
+        if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &stg, &c)) {
+            *idx = fused_find_shape(in_dtype, out_dtype, th, tw, stg);
+            *ctas = c;
+        }
+        if (*idx < 0) *idx = 0;
+        if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
+    }
+    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx);
+    if (maxc <= 0) return fail(SC5_ECUDA, "occupancy query failed for fused shape %d", *idx);
+    if (*ctas <= 0 || *ctas > maxc) *ctas = maxc;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
+{
+    clear_error();
+    if (!desc || !out) return fail(SC5_EINVAL, "null argument");
+    *out = nullptr;
+    const sc5_plan_desc &d = *desc;
+    if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS) return fail(SC5_EINVAL, "unknown algo %d", d.algo);
+    sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
+                                d.in_pitch, d.out_pitch, 1.f, 1.f, false);
+    if (st != SC5_OK) return st;
+    if (!pair_supported(d.in_dtype, d.out_dtype))
+        return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built: the output must be the input format or FP32",
+                    d.in_dtype, d.out_dtype);
+    if (d.algo == SC5_ALGO_TWO_PASS && d.H > 65535) return fail(SC5_EINVAL, "two-pass form needs H <= 65535");
+    sc5_plan p = new (std::nothrow) sc5_plan_s;
+    if (!p) return fail(SC5_ENOMEM, "host allocation failed");
+    p->d = d;
+    cudaGetDevice(&p->device);
+    st = choose_shape(d.in_dtype, d.out_dtype, d.H, d.W, &d, &p->shape_idx, &p->ctas_per_sm);
+    if (st != SC5_OK) {
+        delete p;
+        return st;
+    }
+    fused_shape(d.in_dtype, d.out_dtype, p->shape_idx, &p->shape);
+    if (d.algo == SC5_ALGO_TWO_PASS) {
+        p->t_pitch = (static_cast<int64_t>(d.W - kHalo) + 3) / 4 * 4;
+        const size_t bytes = static_cast<size_t>(d.planes) * d.H * p->t_pitch * sizeof(float);
+        cudaError_t e = cudaMalloc(&p->T, bytes);
+        if (e != cudaSuccess) {
+            delete p;
+            return fail_cuda(e, "cudaMalloc of the two-pass intermediate");
+        }
+    }
+    if (cudaEventCreateWithFlags(&p->ws_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFree(p->T);
+        delete p;
+        return fail(SC5_ECUDA, "cudaEventCreate failed");
+    }
+    *out = p;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_plan_destroy(sc5_plan p)
+{
+    clear_error();
+    if (!p) return SC5_OK;
+    if (p->ws_pending) cudaEventSynchronize(p->ws_done);
+    if (p->s_in) cudaStreamSynchronize(p->s_in);
+    if (p->s_out) cudaStreamSynchronize(p->s_out);
+    cudaFree(p->T);
+    cudaFree(p->ws_dev);
+    cudaFreeHost(p->ws_host);
+    cudaEventDestroy(p->ws_done);
+    cudaFree(p->stage_in);
+    cudaFree(p->stage_out);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    delete p;
+    return SC5_OK;
+}
+
+static sc5_status run_two_pass(sc5_plan p, const void *in, void *out, const float *k, float in_scale,
+                               float out_scale, cudaStream_t st)
+{
+    const sc5_plan_desc &d = p->d;
+    cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, p->T, p->t_pitch, k, st);
+    if (e != cudaSuccess) return fail_cuda(e, "hpass launch");
+    const int eo = dtype_bytes(d.out_dtype);
+    char *ob = static_cast<char *>(out);
+    int64_t plane_rows = d.H - kHalo;
+    if (d.border == SC5_BORDER_KEEP) {
+        ob += (2 * d.out_pitch + 2) * eo;
+        plane_rows = d.H;
+    }
+    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0;
+    const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
+    e = launch_vpass(d.out_dtype, p->T, d.planes, d.H, d.W - kHalo, p->t_pitch, ob, d.out_pitch,
+                     plane_rows * d.out_pitch, k, oscale, vec, st);
+    if (e != cudaSuccess) return fail_cuda(e, "vpass launch");
+    return SC5_OK;
+}
+
+static sc5_status run_frame(const sc5_plan_desc &d, const void *in, void *out, float in_scale,
+                            float out_scale, cudaStream_t st)
+{
+    if (d.border != SC5_BORDER_KEEP) return SC5_OK;
+    const float ratio = static_cast<float>(static_cast<double>(out_scale) / in_scale);
+    cudaError_t e = launch_keep_frame(d.in_dtype, d.out_dtype, in, d.planes, d.H, d.W, d.in_pitch, out,
+                                      d.out_pitch, ratio, st);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "frame launch");
+}
+
+extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const float k[5],
+                                   float in_scale, float out_scale, void *stream)
+{
+    clear_error();
+    if (!p || !k) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
+                                d.out_pitch, in_scale, out_scale, true);
+    if (st != SC5_OK) return st;
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d.algo == SC5_ALGO_TWO_PASS) {
+        st = run_two_pass(p, in, out, k, in_scale, out_scale, s);
+    } else {
+        ImgDesc desc;
+        st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, in, out, d.planes, d.H, d.W,
+                       d.in_pitch, d.out_pitch, k, in_scale, out_scale);
+        if (st != SC5_OK) return st;
+        const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
+        const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
+        cudaError_t e = launch_fused_single(d.in_dtype, d.out_dtype, p->shape_idx, desc, ntiles, grid, s);
+        if (e != cudaSuccess) return fail_cuda(e, "fused launch");
+    }
+    if (st != SC5_OK) return st;
+    return run_frame(d, in, out, in_scale, out_scale, s);
+}
+
+extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *host_out, const float k[5],
+                                        float in_scale, float out_scale, void *stream)
+{
+    clear_error();
+    if (!p || !host_in || !host_out || !k) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W, d.in_pitch,
+                                d.out_pitch, in_scale, out_scale, false);
+    if (st != SC5_OK) return st;
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    const int ei = dtype_bytes(d.in_dtype), eo = dtype_bytes(d.out_dtype);
+    const int Hv = d.H - kHalo;
+    const int64_t hout = d.border == SC5_BORDER_KEEP ? d.H : Hv;
+    const size_t in_row = static_cast<size_t>(d.in_pitch) * ei, out_row = static_cast<size_t>(d.out_pitch) * eo;
+    const size_t in_bytes = in_row * d.H * d.planes, out_bytes = out_row * hout * d.planes;
+    cudaError_t e = cudaSuccess;
+    if (!p->stage_in) e = cudaMalloc(&p->stage_in, in_bytes);
+    if (e == cudaSuccess && !p->stage_out) e = cudaMalloc(&p->stage_out, out_bytes);
+    if (e == cudaSuccess && !p->s_in) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->s_out) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail_cuda(e, "offload staging");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *din = static_cast<char *>(p->stage_in), *dout = static_cast<char *>(p->stage_out);
+    const char *hin = static_cast<const char *>(host_in);
+    char *hout_c = static_cast<char *>(host_out);
+
+    if (d.algo != SC5_ALGO_FUSED || d.border != SC5_BORDER_VALID) {
+        // whole image: copy in, run, copy out
+        e = cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return fail_cuda(e, "copy to device");
+        st = sepconv5_run(p, din, dout, k, in_scale, out_scale, stream);
+        if (st != SC5_OK) return st;
+        e = cudaMemcpyAsync(hout_c, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? SC5_OK : fail_cuda(e, "copy to host");
+    }
+
+    // bands of R output rows (a multiple of the tile height, about 8 per plane)
+    const int th = p->shape.tile_h;
+    const int R = std::max(th, (((Hv + 7) / 8) + th - 1) / th * th);
+    const int nb = (Hv + R - 1) / R;           // output bands per plane
+    const int nc = (d.H + R - 1) / R;          // input chunks per plane
+    const size_t need_ev = static_cast<size_t>(d.planes) * (nc + nb);
+    while (p->ev.size() < need_ev) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail_cuda(e, "event create");
+        p->ev.push_back(ev);
+    }
+    size_t evi = 0;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
+    for (int pl = 0; pl < d.planes; ++pl) {
+        const size_t in_plane = in_row * d.H * pl, out_plane = out_row * Hv * pl;
+        int next_chunk = 0;
+        std::vector<cudaEvent_t> chunk_ev(nc);
+        for (int b = 0; b < nb; ++b) {
+            const int need = std::min(nc - 1, b + 1);
+            while (next_chunk <= need) {
+                const int r0 = next_chunk * R, rows = std::min(d.H - r0, R);
+                const size_t off = in_plane + in_row * r0;
+                e = cudaMemcpyAsync(din + off, hin + off, in_row * rows, cudaMemcpyHostToDevice, p->s_in);
+                if (e != cudaSuccess) return fail_cuda(e, "band copy to device");
+                chunk_ev[next_chunk] = p->ev[evi++];
+                cudaEventRecord(chunk_ev[next_chunk], p->s_in);
+                ++next_chunk;
+            }
+            cudaStreamWaitEvent(s, chunk_ev[need], 0);
+            const int y0 = b * R;
+            const int rows_out = std::min(Hv - y0, R);
+            ImgDesc desc;
+            st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, din + in_plane + in_row * y0,
+                           dout + out_plane + out_row * y0, 1, rows_out + kHalo, d.W, d.in_pitch, d.out_pitch, k,
+                           in_scale, out_scale);
+            if (st != SC5_OK) return st;
+            const int64_t ntiles = static_cast<int64_t>(desc.tiles_x) * desc.tiles_y;
+            const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
+            e = launch_fused_single(d.in_dtype, d.out_dtype, p->shape_idx, desc, ntiles, grid, s);
+            if (e != cudaSuccess) return fail_cuda(e, "band launch");
+            cudaEvent_t kev = p->ev[evi++];
+            cudaEventRecord(kev, s);
+            cudaStreamWaitEvent(p->s_out, kev, 0);
+            const size_t off = out_plane + out_row * y0;
+            e = cudaMemcpyAsync(hout_c + off, dout + off, out_row * rows_out, cudaMemcpyDeviceToHost, p->s_out);
+            if (e != cudaSuccess) return fail_cuda(e, "band copy to host");
+        }
+    }
+    e = cudaStreamSynchronize(p->s_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "offload completion");
+}
+
+extern "C" sc5_status sepconv5_hpass(sc5_plan p, const void *in, float *T, int64_t t_pitch,
+                                     const float k[5], void *stream)
+{
+    clear_error();
+    if (!p || !in || !T || !k) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
+        return fail(SC5_EINVAL, "T needs t_pitch >= W-4, a multiple of 4, and 16-byte alignment");
+    if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
+    if (d.H > 65535) return fail(SC5_EINVAL, "two-pass form needs H <= 65535");
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, T, t_pitch, k,
+                                 static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "hpass launch");
+}
+
+extern "C" sc5_status sepconv5_vpass(sc5_plan p, const float *T, int64_t t_pitch, void *out,
+                                     const float k[5], float in_scale, float out_scale, void *stream)
+{
+    clear_error();
+    if (!p || !out || !T || !k) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
+        return fail(SC5_EINVAL, "T needs t_pitch >= W-4, a multiple of 4, and 16-byte alignment");
+    if (!(in_scale > 0.f) || !(out_scale > 0.f) || !std::isfinite(in_scale) || !std::isfinite(out_scale))
+        return fail(SC5_EINVAL, "scales must be finite and > 0");
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    const int eo = dtype_bytes(d.out_dtype);
+    char *ob = static_cast<char *>(out);
+    int64_t plane_rows = d.H - kHalo;
+    if (d.border == SC5_BORDER_KEEP) {
+        ob += (2 * d.out_pitch + 2) * eo;
+        plane_rows = d.H;
+    }
+    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0;
+    const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
+    cudaError_t e = launch_vpass(d.out_dtype, T, d.planes, d.H, d.W - kHalo, t_pitch, ob, d.out_pitch,
+                                 plane_rows * d.out_pitch, k, oscale, vec, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "vpass launch");
+}
+
+extern "C" sc5_status sepconv5_device_status(void *stream, int32_t *code)
+{
+    clear_error();
+    if (!code) return fail(SC5_EINVAL, "null argument");
+    cudaError_t e = read_and_clear_device_status(static_cast<cudaStream_t>(stream), code);
+    if (e != cudaSuccess) return fail_cuda(e, "reading the device status word");
+    return *code ? fail(SC5_EDEVICE, "a kernel reported device error %d", *code) : SC5_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+namespace sc5 {
+
+// Host-side build of a batch: one ImgDesc per image, tile records in image,
+// plane, row, column order.  Returns the bytes of the device image
+// (descriptors then tiles) in *blob.
+sc5_status build_batch(const sc5_plan_desc &pd, int n, const sc5_image *imgs, const FusedShape &sh,
+                       std::vector<unsigned char> *blob, int64_t *ntiles, size_t *tiles_off)
+{
+    if (n < 1 || !imgs) return fail(SC5_EINVAL, "empty batch");
+    std::vector<ImgDesc> descs(n);
+    int64_t nt = 0;
+    for (int i = 0; i < n; ++i) {
+        const sc5_image &im = imgs[i];
+        sc5_status st = check_image(pd.in_dtype, pd.out_dtype, pd.border, im.in, im.out, pd.planes, im.H, im.W,
+                                    im.in_pitch, im.out_pitch, im.in_scale, im.out_scale, true);
+        if (st != SC5_OK) return fail(st, "image %d: %s", i, sepconv5_last_error());
+        if (!taps_finite(im.k)) return fail(SC5_EINVAL, "image %d: taps must be finite", i);
+        st = fill_desc(&descs[i], pd.in_dtype, pd.out_dtype, pd.border, sh, im.in, im.out, pd.planes, im.H,
+                       im.W, im.in_pitch, im.out_pitch, im.k, im.in_scale, im.out_scale);
+        if (st != SC5_OK) return st;
+        nt += static_cast<int64_t>(pd.planes) * descs[i].tiles_x * descs[i].tiles_y;
+    }
+    const size_t dbytes = sizeof(ImgDesc) * n;
+    const size_t toff = (dbytes + 255) / 256 * 256;
+    blob->assign(toff + sizeof(TileRec) * nt, 0);
+    std::memcpy(blob->data(), descs.data(), dbytes);
+    TileRec *t = reinterpret_cast<TileRec *>(blob->data() + toff);
+    for (int i = 0; i < n; ++i)
+        for (int p = 0; p < pd.planes; ++p)
+            for (int ty = 0; ty < descs[i].tiles_y; ++ty)
+                for (int tx = 0; tx < descs[i].tiles_x; ++tx) *t++ = TileRec{i, p, ty, tx};
+    *ntiles = nt;
+    *tiles_off = toff;
+    return SC5_OK;
+}
+
+// Shape for a batch: the plan's override, else the tuned choice for the size
+// class holding the most pixels.
+sc5_status batch_shape(sc5_plan p, int n, const sc5_image *imgs, int *idx, int *ctas)
+{
+    const sc5_plan_desc &d = p->d;
+    if (d.tile_h || d.tile_w || d.stages) {
+        *idx = p->shape_idx;
+        *ctas = p->ctas_per_sm;
+        return SC5_OK;
+    }
+    double by_class[64] = {};
+    for (int i = 0; i < n; ++i) {
+        const double px = static_cast<double>(imgs[i].H) * imgs[i].W;
+        const int c = std::min(63, std::max(0, static_cast<int>(std::log2(std::max(1.0, px)))));
+        by_class[c] += px;
+    }
+    const int best = static_cast<int>(std::max_element(by_class, by_class + 64) - by_class);
+    const int side = 1 << (best / 2);
+    const int H = side, W = (best % 2) ? side * 2 : side;
+    *idx = -1;
+    *ctas = 0;
+    return choose_shape(d.in_dtype, d.out_dtype, H, W, d.ctas_per_sm ? &d : nullptr, idx, ctas);
+}
+
+}  // namespace sc5
+
+extern "C" sc5_status sepconv5_run_batch(sc5_plan p, int32_t n, const sc5_image *imgs, void *stream)
+{
+    clear_error();
+    if (!p) return fail(SC5_EINVAL, "null plan");
+    if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
+    int idx = 0, ctas = 1;
+    sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
+    if (st != SC5_OK) return st;
+    FusedShape sh;
+    fused_shape(p->d.in_dtype, p->d.out_dtype, idx, &sh);
+    std::vector<unsigned char> blob;
+    int64_t ntiles = 0;
+    size_t toff = 0;
+    st = build_batch(p->d, n, imgs, sh, &blob, &ntiles, &toff);
+    if (st != SC5_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the pinned staging buffer may still feed an earlier upload
+    if (p->ws_pending) {
+        cudaEventSynchronize(p->ws_done);
+        p->ws_pending = false;
+    }
+    if (blob.size() > p->ws_cap) {
+        cudaStreamSynchronize(s);
+        cudaFree(p->ws_dev);
+        p->ws_dev = nullptr;
+        p->ws_cap = 0;
+        cudaError_t e = cudaMalloc(&p->ws_dev, blob.size());
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc of the batch work-list");
+        p->ws_cap = blob.size();
+    }
+    if (blob.size() > p->ws_host_cap) {
+        cudaFreeHost(p->ws_host);
+        p->ws_host = nullptr;
+        p->ws_host_cap = 0;
+        cudaError_t e = cudaMallocHost(&p->ws_host, blob.size());
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMallocHost of the batch staging buffer");
+        p->ws_host_cap = blob.size();
+    }
+    std::memcpy(p->ws_host, blob.data(), blob.size());
+    cudaError_t e = cudaMemcpyAsync(p->ws_dev, p->ws_host, blob.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "work-list upload");
+    cudaEventRecord(p->ws_done, s);
+    p->ws_pending = true;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * ctas;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
+    e = launch_fused_batch(p->d.in_dtype, p->d.out_dtype, idx, reinterpret_cast<const ImgDesc *>(p->ws_dev),
+                           reinterpret_cast<const TileRec *>(p->ws_dev + toff), ntiles, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "batch launch");
+    if (p->d.border == SC5_BORDER_KEEP) {
+        for (int i = 0; i < n; ++i) {
+            sc5_plan_desc fd = p->d;
+            fd.H = imgs[i].H;
+            fd.W = imgs[i].W;
+            fd.in_pitch = imgs[i].in_pitch;
+            fd.out_pitch = imgs[i].out_pitch;
+            st = run_frame(fd, imgs[i].in, imgs[i].out, imgs[i].in_scale, imgs[i].out_scale, s);
+            if (st != SC5_OK) return st;
+        }
+    }
+    return SC5_OK;
+}
+
+struct sc5_batch_s {
+    int device = 0;
+    unsigned char *ws = nullptr;
+    int64_t ntiles = 0;
+    int grid = 0;
+    FusedShape shape{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_image *imgs, sc5_batch *out)
+{
+    clear_error();
+    if (!p || !out) return fail(SC5_EINVAL, "null argument");
+    *out = nullptr;
+    if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
+    int idx = 0, ctas = 1;
+    sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
+    if (st != SC5_OK) return st;
+    sc5_batch b = new (std::nothrow) sc5_batch_s;
+    if (!b) return fail(SC5_ENOMEM, "host allocation failed");
+    cudaGetDevice(&b->device);
+    fused_shape(p->d.in_dtype, p->d.out_dtype, idx, &b->shape);
+    std::vector<unsigned char> blob;
+    size_t toff = 0;
+    st = build_batch(p->d, n, imgs, b->shape, &blob, &b->ntiles, &toff);
+    if (st != SC5_OK) {
+        delete b;
+        return st;
+    }
+    cudaError_t e = cudaMalloc(&b->ws, blob.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->ws, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = fused_prepare(p->d.in_dtype, p->d.out_dtype, idx);
+    const int64_t cap = static_cast<int64_t>(num_sms()) * ctas;
+    b->grid = static_cast<int>(std::max<int64_t>(1, std::min(b->ntiles, cap)));
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = launch_fused_batch(p->d.in_dtype, p->d.out_dtype, idx,
+                                            reinterpret_cast<const ImgDesc *>(b->ws),
+                                            reinterpret_cast<const TileRec *>(b->ws + toff), b->ntiles,
+                                            b->grid, cs);
+        if (le == cudaSuccess && p->d.border == SC5_BORDER_KEEP) {
+            for (int i = 0; i < n && le == cudaSuccess; ++i) {
+                const float ratio = static_cast<float>(static_cast<double>(imgs[i].out_scale) / imgs[i].in_scale);
+                le = launch_keep_frame(p->d.in_dtype, p->d.out_dtype, imgs[i].in, p->d.planes, imgs[i].H,
+                                       imgs[i].W, imgs[i].in_pitch, imgs[i].out, imgs[i].out_pitch, ratio, cs);
+            }
+        }
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (b->graph) cudaGraphDestroy(b->graph);
+        cudaFree(b->ws);
+        delete b;
+        return fail_cuda(e, "batch graph capture");
+    }
+    *out = b;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_batch_launch(sc5_batch b, void *stream)
+{
+    clear_error();
+    if (!b) return fail(SC5_EINVAL, "null batch");
+    cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "graph launch");
+    note_launches(1);
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_batch_info(sc5_batch b, int64_t *tiles, int32_t *ctas, int32_t *tile_h,
+                                          int32_t *tile_w)
+{
+    clear_error();
+    if (!b) return fail(SC5_EINVAL, "null batch");
+    if (tiles) *tiles = b->ntiles;
+    if (ctas) *ctas = b->grid;
+    if (tile_h) *tile_h = b->shape.tile_h;
+    if (tile_w) *tile_w = b->shape.tile_w;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_batch_destroy(sc5_batch b)
+{
+    clear_error();
+    if (!b) return SC5_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->ws);
+    delete b;
+    return SC5_OK;
+}
+
+// ------------------------------------------------------------------ misc
+
+extern "C" sc5_status sepconv5_fused_configs(int32_t in_dtype, int32_t out_dtype, int32_t *cfg, int32_t cap,
+                                             int32_t *n)
+{
+    clear_error();
+    if (!n) return fail(SC5_EINVAL, "null argument");
+    const int m = fused_num_shapes(in_dtype, out_dtype);
+    *n = m;
+    for (int i = 0; i < m && i < cap && cfg; ++i) {
+        FusedShape s;
+        fused_shape(in_dtype, out_dtype, i, &s);
+        cfg[3 * i] = s.tile_h;
+        cfg[3 * i + 1] = s.tile_w;
+        cfg[3 * i + 2] = s.stages;
+    }
+    return m ? SC5_OK : fail(SC5_EINVAL, "dtype pair not built");
+}
+
+extern "C" const char *sepconv5_last_error(void) { return t_err.c_str(); }
+
+extern "C" sc5_status sepconv5_empty_launches(int32_t n, void *stream)
+{
+    clear_error();
+    cudaError_t e = launch_empty(n, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "empty launch");
+}
+
+extern "C" int64_t sepconv5_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,19 @@
+// sc5_fused_f32.cu -- fused-kernel instantiations for FP32 storage.
+#include "sc5_fused_impl.cuh"
+
+namespace sc5 {
+
+int fused_entries_f32(int out_dtype, const FusedEntry **out)
+{
+    // (tile_h, tile_w, rows per thread, stages)
+    static const FusedEntry f32_f32[] = {
+        make_entry<float, float, 64, 128, 8, 4>(),
+        make_entry<float, float, 32, 128, 4, 5>(),
+        make_entry<float, float, 128, 128, 16, 3>(),
+        make_entry<float, float, 64, 128, 8, 2>(),
+    };
+    if (out_dtype == SC5_F32) { *out = f32_f32; return 4; }
+    return 0;
+}
+
+}  // namespace sc5

@@ -1,0 +1,23 @@
+// sc5_fused_fp8.cu -- fused-kernel instantiations for FP8 E4M3 storage
+// (output in E4M3 or in FP32).
+#include "sc5_fused_impl.cuh"
+
+namespace sc5 {
+
+#define SC5_SHAPES_8(TI, TO)                                    \
+    {                                                           \
+        make_entry<TI, TO, 128, 128, 16, 6>(),                  \
+        make_entry<TI, TO, 64, 128, 8, 8>(),                    \
+        make_entry<TI, TO, 128, 128, 16, 3>(),                  \
+    }
+
+int fused_entries_fp8(int out_dtype, const FusedEntry **out)
+{
+    static const FusedEntry e_e[] = SC5_SHAPES_8(fp8e4m3_t, fp8e4m3_t);
+    static const FusedEntry e_f32[] = SC5_SHAPES_8(fp8e4m3_t, float);
+    if (out_dtype == SC5_FP8E4M3) { *out = e_e; return 3; }
+    if (out_dtype == SC5_F32) { *out = e_f32; return 3; }
+    return 0;
+}
+
+}  // namespace sc5

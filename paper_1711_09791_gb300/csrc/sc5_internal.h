@@ -1,0 +1,80 @@
+// sc5_internal.h -- declarations shared by the translation units of
+// libsepconv5 (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sepconv5.h"
+
+namespace sc5 {
+
+constexpr int kTaps = 5;
+constexpr int kHalo = 4;          // a width-5 kernel needs 2 extra pixels per side
+constexpr int kColsPerThread = 4; // output columns per consumer thread
+
+// Error codes written to the device status word.
+constexpr int kDevErrTmaTimeout = 1;
+
+// Per-image description read by the fused kernels.  The tensor map describes
+// the input image as a 3-D tensor (x = column, y = row, z = plane).
+struct alignas(64) ImgDesc {
+    CUtensorMap tmap;      // 128 bytes
+    void *out;             // first VALID output pixel (plane 0)
+    int64_t out_pitch;     // elements
+    int64_t out_plane;     // elements between planes
+    int32_t Hv, Wv;        // VALID output rows / cols
+    int32_t tiles_x, tiles_y;
+    float k[kTaps];
+    float oscale;          // out_scale / in_scale
+    int32_t vec;           // 1: 4-wide vector stores are aligned
+    int32_t pad_[5];
+};
+static_assert(sizeof(ImgDesc) % 64 == 0, "ImgDesc must keep the tensor map 64-byte aligned");
+
+// One entry of a batch work-list: a (th x tw) output tile of one plane.
+struct TileRec {
+    int32_t img, plane, ty, tx;
+};
+
+// A compiled fused-kernel shape.
+struct FusedShape {
+    int tile_h, tile_w, rows_per_thread, stages;
+};
+
+// Fused kernel launchers (sc5_fused.cu).  Return a cudaError_t.
+int fused_num_shapes(int in_dtype, int out_dtype);
+bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s);
+int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages);
+// Bytes of dynamic shared memory and threads per CTA of a shape.
+int fused_smem_bytes(int in_dtype, const FusedShape &s);
+int fused_threads(const FusedShape &s);
+// Max resident CTAs per SM for a shape (occupancy query), or <= 0 on error.
+int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx);
+// Set the kernel attributes of a shape on the current device (call before
+// capturing a launch into a graph).
+cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx);
+cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgDesc &d,
+                                int64_t ntiles, int grid, cudaStream_t st);
+cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDesc *descs,
+                               const TileRec *tiles, int64_t ntiles, int grid, cudaStream_t st);
+cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code);
+
+// Two-pass kernels and helpers (sc5_twopass.cu).
+cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,
+                         float *T, int64_t t_pitch, const float *k, cudaStream_t st);
+cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, int64_t t_pitch,
+                         void *out, int64_t out_pitch, int64_t out_plane, const float *k,
+                         float oscale, bool vec, cudaStream_t st);
+cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
+                              int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
+                              cudaStream_t st);
+cudaError_t launch_empty(int n, cudaStream_t st);
+
+// Library-wide helpers (sc5_api.cu).
+void note_launches(int64_t n);
+int dtype_bytes(int dtype);
+int num_sms();
+
+}  // namespace sc5

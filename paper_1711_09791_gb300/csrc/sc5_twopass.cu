@@ -1,0 +1,245 @@
+// sc5_twopass.cu -- the two-pass kernel pair (Sec. 5.1; Listing 1 and
+// Listing 2 of the paper compute the same two passes on the Xeon Phi), the
+// border-frame copy and the empty launch-overhead probe.
+//
+//   hpass:  T[p][y][x] = sum_t k[t] * A[p][y][x+t]      all rows y in [0, H),
+//           x in [0, W-4)  (input column x+2 is the centre; the paper's
+//           OpenCL pass has no row guard, so every row of T is defined)
+//   vpass:  B[p][y][x] = sum_t k[t] * T[p][y+t][x]      y in [0, H-4)
+//
+// T is FP32 in HBM, so every plane-pixel is read twice and written twice
+// (the paper's "two assignment operations", Sec. 7).  The arithmetic order is
+// the one of the fused kernel (hdot, then taps t = 0..4 of the column pass,
+// then the output scale), so both forms give identical bits.
+#include "sc5_device.cuh"
+
+namespace sc5 {
+
+struct Taps {
+    float k[kTaps];
+};
+
+constexpr int kPassThreads = 128;
+constexpr int kVRows = 8;  // output rows per thread in the vertical pass
+
+template <class TIn>
+__global__ void __launch_bounds__(kPassThreads)
+hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, float *__restrict__ T,
+             int64_t t_pitch, Taps taps)
+{
+    const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
+    const int Wv = W - kHalo;
+    if (x >= Wv) return;
+    const int y = blockIdx.y, p = blockIdx.z;
+    const TIn *row = in + (static_cast<int64_t>(p) * H + y) * in_pitch + x;
+    float k[kTaps];
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
+    float a[8];
+    if (x + 8 <= W) {
+        Fmt<TIn>::load8(row, a);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = (x + j < W) ? Fmt<TIn>::load1(row + j) : 0.f;
+    }
+    float h[kColsPerThread];
+#pragma unroll
+    for (int c = 0; c < kColsPerThread; ++c) h[c] = hdot(k, a + c);
+    float *dst = T + (static_cast<int64_t>(p) * H + y) * t_pitch + x;
+    if (x + kColsPerThread <= Wv) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(h[0], h[1], h[2], h[3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < kColsPerThread; ++c)
+            if (x + c < Wv) dst[c] = h[c];
+    }
+}
+
+template <class TOut>
+__global__ void __launch_bounds__(kPassThreads)
+vpass_kernel(const float *__restrict__ T, int H, int Wv, int64_t t_pitch, TOut *__restrict__ out,
+             int64_t out_pitch, int64_t out_plane, Taps taps, float oscale, int vec)
+{
+    const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
+    if (x >= Wv) return;
+    const int Hv = H - kHalo;
+    const int y0 = blockIdx.y * kVRows, p = blockIdx.z;
+    const int rows_valid = min(kVRows, Hv - y0);
+    const int cols_valid = min(kColsPerThread, Wv - x);
+    float k[kTaps];
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
+    const float *src = T + (static_cast<int64_t>(p) * H + y0) * t_pitch + x;
+    TOut *dst0 = out + p * out_plane + static_cast<int64_t>(y0) * out_pitch + x;
+    float acc[kVRows][kColsPerThread];
+#pragma unroll
+    for (int r = 0; r < kVRows + kHalo; ++r) {
+        float v[kColsPerThread] = {0.f, 0.f, 0.f, 0.f};
+        if (y0 + r < H) {
+            const float4 q = *reinterpret_cast<const float4 *>(src + static_cast<int64_t>(r) * t_pitch);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        }
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+            const int o = r - t;
+            if (o >= 0 && o < kVRows) {
+#pragma unroll
+                for (int c = 0; c < kColsPerThread; ++c)
+                    acc[o][c] = (t == 0) ? __fmul_rn(k[0], v[c]) : __fmaf_rn(k[t], v[c], acc[o][c]);
+            }
+        }
+        const int o = r - kHalo;
+        if (o >= 0 && o < rows_valid) {
+            float w[kColsPerThread];
+#pragma unroll
+            for (int c = 0; c < kColsPerThread; ++c) w[c] = __fmul_rn(acc[o][c], oscale);
+            TOut *dst = dst0 + static_cast<int64_t>(o) * out_pitch;
+            if (vec && cols_valid == kColsPerThread) {
+                Fmt<TOut>::store4(dst, w);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kColsPerThread; ++c)
+                    if (c < cols_valid) Fmt<TOut>::store1(dst + c, w[c]);
+            }
+        }
+    }
+}
+
+// The 2-pixel frame of a KEEP-border output: out = value(in) * ratio, stored
+// in the output format (an exact copy when formats and scales agree).
+template <class TIn, class TOut>
+__global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch,
+                                  TOut *__restrict__ out, int64_t out_pitch, float ratio)
+{
+    const int64_t n_rows = 4ll * W;                 // rows 0, 1, H-2, H-1
+    const int64_t n = n_rows + 4ll * (H - kHalo);   // plus cols 0, 1, W-2, W-1 of rows 2..H-3
+    const int p = blockIdx.y;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        int y, x;
+        if (i < n_rows) {
+            const int r = static_cast<int>(i / W);
+            y = (r < 2) ? r : H - 4 + r;
+            x = static_cast<int>(i % W);
+        } else {
+            const int64_t j = i - n_rows;
+            y = 2 + static_cast<int>(j / 4);
+            const int c = static_cast<int>(j % 4);
+            x = (c < 2) ? c : W - 4 + c;
+        }
+        const float v = Fmt<TIn>::load1(in + (static_cast<int64_t>(p) * H + y) * in_pitch + x);
+        Fmt<TOut>::store1(out + (static_cast<int64_t>(p) * H + y) * out_pitch + x, __fmul_rn(v, ratio));
+    }
+}
+
+__global__ void empty_kernel() {}
+
+// ------------------------------------------------------------------ launchers
+
+static Taps make_taps(const float *k)
+{
+    Taps t;
+    for (int i = 0; i < kTaps; ++i) t.k[i] = k[i];
+    return t;
+}
+
+cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,
+                         float *T, int64_t t_pitch, const float *k, cudaStream_t st)
+{
+    const int Wv = W - kHalo;
+    const int groups = (Wv + kColsPerThread - 1) / kColsPerThread;
+    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, H, P);
+    const Taps taps = make_taps(k);
+    switch (in_dtype) {
+    case SC5_F32:
+        hpass_kernel<float><<<grid, kPassThreads, 0, st>>>(static_cast<const float *>(in), H, W, in_pitch, T, t_pitch, taps);
+        break;
+    case SC5_BF16:
+        hpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const bf16_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        break;
+    case SC5_F16:
+        hpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const f16_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        break;
+    case SC5_FP8E4M3:
+        hpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(static_cast<const fp8e4m3_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) note_launches(1);
+    return err;
+}
+
+cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, int64_t t_pitch,
+                         void *out, int64_t out_pitch, int64_t out_plane, const float *k,
+                         float oscale, bool vec, cudaStream_t st)
+{
+    const int Hv = H - kHalo;
+    const int groups = (Wv + kColsPerThread - 1) / kColsPerThread;
+    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, (Hv + kVRows - 1) / kVRows, P);
+    const Taps taps = make_taps(k);
+    const int v = vec ? 1 : 0;
+    switch (out_dtype) {
+    case SC5_F32:
+        vpass_kernel<float><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<float *>(out), out_pitch, out_plane, taps, oscale, v);
+        break;
+    case SC5_BF16:
+        vpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<bf16_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        break;
+    case SC5_F16:
+        vpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<f16_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        break;
+    case SC5_FP8E4M3:
+        vpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) note_launches(1);
+    return err;
+}
+
+template <class TIn>
+static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, int64_t in_pitch,
+                             void *out, int64_t out_pitch, float ratio, cudaStream_t st)
+{
+    const int64_t n = 4ll * W + 4ll * (H - kHalo);
+    const dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), P);
+    switch (out_dtype) {
+    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<float *>(out), out_pitch, ratio); break;
+    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<bf16_t *>(out), out_pitch, ratio); break;
+    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<f16_t *>(out), out_pitch, ratio); break;
+    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<fp8e4m3_t *>(out), out_pitch, ratio); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
+                              int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
+                              cudaStream_t st)
+{
+    cudaError_t err;
+    switch (in_dtype) {
+    case SC5_F32: err = frame_out(out_dtype, static_cast<const float *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
+    case SC5_BF16: err = frame_out(out_dtype, static_cast<const bf16_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
+    case SC5_F16: err = frame_out(out_dtype, static_cast<const f16_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
+    case SC5_FP8E4M3: err = frame_out(out_dtype, static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (err == cudaSuccess) note_launches(1);
+    return err;
+}
+
+cudaError_t launch_empty(int n, cudaStream_t st)
+{
+    for (int i = 0; i < n; ++i) {
+        empty_kernel<<<1, 32, 0, st>>>();
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        note_launches(1);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sc5
