@@ -84,12 +84,13 @@ def test_ragged_shapes_every_fused_shape(sc5, H, W):
 def test_shifted_delta_kernels_exact(sc5, algo):
     """k = e_t moves the image by t-2 on both axes, exactly (pins orientation)."""
     P, H, W = 3, 70, 133
-    A = synth.image(5, H, W)
+    pitch = U.pitch_for(W, "f32")
+    A = synth.image(5, H, W, pitch=pitch)
     A_dev = U.to_dev(A)
     for t in range(5):
         k = np.zeros(5, np.float32)
         k[t] = 1.0
-        out, _ = _run(sc5, A_dev, P, H, W, W, k, algo=algo, out_pitch=W - 4)
+        out, _ = _run(sc5, A_dev, P, H, W, pitch, k, algo=algo, out_pitch=W - 4)
         assert np.array_equal(out, A[:, t:t + H - 4, t:t + W - 4]), t
 
 
@@ -101,7 +102,10 @@ def test_exact_integers_bitwise(sc5, algo):
     A = synth.integer_image(9, H, W)
     k = np.array([1, 4, 6, 4, 1], np.float32)
     ref = oracle.direct(A.astype(np.float64), k.astype(np.float64))
-    out, _ = _run(sc5, U.to_dev(A), P, H, W, W, k, algo=algo, out_pitch=W - 4)
+    pitch = U.pitch_for(W, "f32")
+    Ap = np.zeros((P, H, pitch), np.float32)
+    Ap[:, :, :W] = A
+    out, _ = _run(sc5, U.to_dev(Ap), P, H, W, pitch, k, algo=algo, out_pitch=W - 4)
     assert np.array_equal(out.astype(np.float64), ref)
 
 
@@ -136,10 +140,12 @@ def test_hpass_and_vpass_separately(sc5):
 def test_keep_border(sc5, algo):
     """KEEP: the 2-pixel frame is the input, the interior the VALID result."""
     P, H, W = 3, 77, 150
-    A = synth.image(21, H, W)
+    pitch = U.pitch_for(W, "f32")
+    Ap = synth.image(21, H, W, pitch=pitch)
+    A = np.ascontiguousarray(Ap[:, :, :W])
     k = synth.kernel_normalised(21)
     ref = oracle.keep_frame(A.astype(np.float64), oracle.direct(A.astype(np.float64), k.astype(np.float64)))
-    out, _ = _run(sc5, U.to_dev(A), P, H, W, W, k, algo=algo, border="keep", out_pitch=W)
+    out, _ = _run(sc5, U.to_dev(Ap), P, H, W, pitch, k, algo=algo, border="keep", out_pitch=W)
     frame = np.ones((H, W), bool)
     frame[2:-2, 2:-2] = False
     assert np.array_equal(out[:, frame], A[:, frame])
