@@ -165,6 +165,37 @@ SC5_API sc5_status sepconv5_hpass(sc5_plan plan, const void *in, float *T, int64
 SC5_API sc5_status sepconv5_vpass(sc5_plan plan, const float *T, int64_t t_pitch, void *out,
                           const float k[5], float in_scale, float out_scale, void *stream);
 
+/* Two-pass form that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory, such
+ * as code running under a framework whose caching allocator owns the GPU's
+ * memory, latency-bound loops that cannot absorb the device-wide
+ * synchronisation a cudaFree may cause, or plug-ins whose host forbids
+ * allocation calls.  It computes exactly what a SC5_ALGO_TWO_PASS plan with
+ * SC5_BORDER_VALID computes (same kernels, same bits), but its FP32
+ * intermediate lives in a fixed array inside the library instead of a
+ * plan's workspace:
+ *   - every GPU that loads the library holds that array
+ *     (SC5_NOALLOC_MAX_T_FLOATS floats = 16 MiB) until the process exits;
+ *   - planes * H * round_up(W-4, 4) must not exceed SC5_NOALLOC_MAX_T_FLOATS
+ *     (e.g. 3 planes of 1152 x 1152), else SC5_EINVAL with a message; H <= 65535;
+ *   - the first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture;
+ *   - it calls no cudaMalloc, cudaFree or other allocating routine;
+ *   - all calls share the one array and it keeps the last call's contents;
+ *     nothing in it has to start at zero (each call writes every element it
+ *     reads), but calls that overlap on the GPU (e.g. on two streams at once)
+ *     race on it and must be serialised by the caller.
+ * Arguments: in / out are dev pointers laid out as for sepconv5_run with
+ * SC5_BORDER_VALID (input 16-byte aligned, in_pitch * element size a
+ * multiple of 16); dtype pair, k and scales as for sepconv5_plan /
+ * sepconv5_run.  Asynchronous on `stream`. */
+#define SC5_NOALLOC_MAX_T_FLOATS 4194304
+SC5_API sc5_status sepconv5_two_pass_noalloc(const void *in, void *out, int32_t planes, int32_t H, int32_t W,
+                                             int64_t in_pitch, int64_t out_pitch, int32_t in_dtype,
+                                             int32_t out_dtype, const float k[5], float in_scale,
+                                             float out_scale, void *stream);
+
 /* Synchronise `stream`, then read and clear the device status word shared by
  * every kernel of this library on the current device: 0 if no kernel
  * reported an error since the last call, else SC5_EDEVICE with *code set to
