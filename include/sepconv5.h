@@ -263,6 +263,9 @@ typedef struct {
     int32_t n_streams;        /* compute streams used round robin (>= 1) */
     int32_t max_merge;        /* most requests merged into one launch (0 = no limit) */
     int32_t merge;            /* 1 = continuous batching, 0 = one launch per request */
+    int32_t batch_window_us;  /* hold admitted requests up to this long (or until max_merge
+                                 are waiting) before launching them together; 0 = launch
+                                 whatever is admitted as soon as a stream slot is free */
 } sc5_serve_cfg;
 
 typedef struct {

@@ -212,8 +212,8 @@ struct sc5_plan_s {
     std::vector<cudaEvent_t> ev;
 };
 
-static sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov,
-                               int *idx, int *ctas)
+namespace sc5 {
+sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas)
 {
     if (ov && (ov->tile_h || ov->tile_w || ov->stages)) {
         const int i = fused_find_shape(in_dtype, out_dtype, ov->tile_h ? ov->tile_h : 64,
@@ -236,6 +236,7 @@ static sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const 
     if (*ctas <= 0 || *ctas > maxc) *ctas = maxc;
     return SC5_OK;
 }
+}  // namespace sc5
 
 extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
 {
@@ -537,16 +538,9 @@ sc5_status build_batch(const sc5_plan_desc &pd, int n, const sc5_image *imgs, co
     return SC5_OK;
 }
 
-// Shape for a batch: the plan's override, else the tuned choice for the size
-// class holding the most pixels.
-sc5_status batch_shape(sc5_plan p, int n, const sc5_image *imgs, int *idx, int *ctas)
+sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas)
 {
-    const sc5_plan_desc &d = p->d;
-    if (d.tile_h || d.tile_w || d.stages) {
-        *idx = p->shape_idx;
-        *ctas = p->ctas_per_sm;
-        return SC5_OK;
-    }
+    if (n < 1 || !imgs) return fail(SC5_EINVAL, "empty batch");
     double by_class[64] = {};
     for (int i = 0; i < n; ++i) {
         const double px = static_cast<double>(imgs[i].H) * imgs[i].W;
@@ -557,8 +551,22 @@ sc5_status batch_shape(sc5_plan p, int n, const sc5_image *imgs, int *idx, int *
     const int side = 1 << (best / 2);
     const int H = side, W = (best % 2) ? side * 2 : side;
     *idx = -1;
-    *ctas = 0;
-    return choose_shape(d.in_dtype, d.out_dtype, H, W, d.ctas_per_sm ? &d : nullptr, idx, ctas);
+    return choose_shape(in_dtype, out_dtype, H, W, nullptr, idx, ctas);
+}
+
+// Shape for a batch: the plan's override, else the tuned choice for the size
+// class holding the most pixels.
+sc5_status batch_shape(sc5_plan p, int n, const sc5_image *imgs, int *idx, int *ctas)
+{
+    const sc5_plan_desc &d = p->d;
+    if (d.tile_h || d.tile_w || d.stages) {
+        *idx = p->shape_idx;
+        *ctas = p->ctas_per_sm;
+        return SC5_OK;
+    }
+    sc5_status st = choose_batch_shape(d.in_dtype, d.out_dtype, n, imgs, idx, ctas);
+    if (st == SC5_OK && d.ctas_per_sm) *ctas = std::min(*ctas, d.ctas_per_sm);
+    return st;
 }
 
 }  // namespace sc5

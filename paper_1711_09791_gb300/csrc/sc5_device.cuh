@@ -173,12 +173,13 @@ template <> struct Fmt<bf16_t> {
     static constexpr int bytes = 2;
     __device__ static __forceinline__ void load8(const bf16_t *p, float (&a)[8])
     {
+        // a bfloat16 is the upper half of a binary32: one shift or mask per element
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
         const uint2 v = *reinterpret_cast<const uint2 *>(p + 4);
-        a[0] = bf16_bits_to_f32(u.x & 0xffffu); a[1] = bf16_bits_to_f32(u.x >> 16);
-        a[2] = bf16_bits_to_f32(u.y & 0xffffu); a[3] = bf16_bits_to_f32(u.y >> 16);
-        a[4] = bf16_bits_to_f32(v.x & 0xffffu); a[5] = bf16_bits_to_f32(v.x >> 16);
-        a[6] = bf16_bits_to_f32(v.y & 0xffffu); a[7] = bf16_bits_to_f32(v.y >> 16);
+        a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xffff0000u);
+        a[2] = __uint_as_float(u.y << 16); a[3] = __uint_as_float(u.y & 0xffff0000u);
+        a[4] = __uint_as_float(v.x << 16); a[5] = __uint_as_float(v.x & 0xffff0000u);
+        a[6] = __uint_as_float(v.y << 16); a[7] = __uint_as_float(v.y & 0xffff0000u);
     }
     __device__ static __forceinline__ float load1(const bf16_t *p) { return bf16_bits_to_f32(p->v); }
     __device__ static __forceinline__ void store4(bf16_t *p, const float (&r)[4])
@@ -251,6 +252,38 @@ template <> struct Fmt<fp8e4m3_t> {
         p->v = static_cast<uint8_t>(f32x2_to_e4m3x2(r, 0.f) & 0xffu);
     }
 };
+
+// ------------------------------------------------------------------ packed FP32 pairs
+// Blackwell executes two IEEE binary32 multiply-adds per instruction on a
+// register pair (fma.rn.f32x2); each half is rounded exactly as the scalar
+// fmaf would round it, so packed and scalar code give the same bits.
+
+__device__ __forceinline__ uint64_t pack2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// a * b + c, element-wise on pairs
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // ------------------------------------------------------------------ arithmetic
 // The two 1D passes, with the taps applied in the fixed order t = 0..4

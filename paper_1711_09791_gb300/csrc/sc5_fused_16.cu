@@ -6,9 +6,11 @@ namespace sc5 {
 
 #define SC5_SHAPES_16(TI, TO)                                   \
     {                                                           \
-        make_entry<TI, TO, 64, 128, 8, 6>(),                    \
-        make_entry<TI, TO, 128, 128, 16, 4>(),                  \
-        make_entry<TI, TO, 64, 128, 8, 3>(),                    \
+        make_entry<TI, TO, 64, 128, 4, 6>(),                    \
+        make_entry<TI, TO, 128, 128, 8, 4>(),                   \
+        make_entry<TI, TO, 64, 128, 4, 4>(),                    \
+        make_entry<TI, TO, 32, 128, 2, 8>(),                    \
+        make_entry<TI, TO, 128, 128, 8, 3>(),                   \
     }
 
 int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
@@ -17,10 +19,10 @@ int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
     static const FusedEntry bf_f32[] = SC5_SHAPES_16(bf16_t, float);
     static const FusedEntry h_h[] = SC5_SHAPES_16(f16_t, f16_t);
     static const FusedEntry h_f32[] = SC5_SHAPES_16(f16_t, float);
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) { *out = bf_bf; return 3; }
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) { *out = bf_f32; return 3; }
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) { *out = h_h; return 3; }
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) { *out = h_f32; return 3; }
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) { *out = bf_bf; return 5; }
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) { *out = bf_f32; return 5; }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) { *out = h_h; return 5; }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) { *out = h_f32; return 5; }
     return 0;
 }
 

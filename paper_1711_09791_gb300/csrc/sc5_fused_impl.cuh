@@ -46,34 +46,54 @@ __host__ __device__ constexpr int fused_stage_bytes()
 // One lane's strip: R output rows x 4 output columns.
 //   s:   shared memory at (first input row of the strip, first input column)
 //   out: global memory at (first output row, first output column)
+//   kk:  the taps as pairs (k[t], k[t]); os2 = (oscale, oscale)
+// Columns are processed as two pairs, (0,1) and (2,3), with packed FP32
+// arithmetic.  For column pair (c, c+1), tap t multiplies the input pair
+// (a[c+t], a[c+t+1]): even t gives the aligned pairs E = (a0,a1), (a2,a3), ...,
+// odd t the shifted pairs O = (a1,a2), (a3,a4), (a5,a6).  Per element this is
+// exactly hdot's sequence: k0*a0, then fused multiply-adds for t = 1..4.
 template <class TIn, class TOut, int R, int BW>
-__device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const float (&k)[kTaps],
-                                           float oscale, TOut *__restrict__ out, int64_t out_pitch,
-                                           int rows_valid, int cols_valid, bool vec)
+__device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps],
+                                           uint64_t os2, bool scaled, TOut *__restrict__ out,
+                                           int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
 {
-    float acc[R][kColsPerThread];
+    uint64_t accL[R], accR[R];
 #pragma unroll
     for (int r = 0; r < R + kHalo; ++r) {
         float a[8];
         Fmt<TIn>::load8(s + r * BW, a);
-        float h[kColsPerThread];
-#pragma unroll
-        for (int c = 0; c < kColsPerThread; ++c) h[c] = hdot(k, a + c);
+        const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
+        const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
+        const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
+        uint64_t hL = mul2(kk[0], E0);
+        hL = fma2(kk[1], O0, hL);
+        hL = fma2(kk[2], E1, hL);
+        hL = fma2(kk[3], O1, hL);
+        hL = fma2(kk[4], E2, hL);
+        uint64_t hR = mul2(kk[0], E1);
+        hR = fma2(kk[1], O1, hR);
+        hR = fma2(kk[2], E2, hR);
+        hR = fma2(kk[3], O2, hR);
+        hR = fma2(kk[4], E3, hR);
         // input row r carries tap t = r - o of output row o
 #pragma unroll
         for (int t = 0; t < kTaps; ++t) {
             const int o = r - t;
             if (o >= 0 && o < R) {
-#pragma unroll
-                for (int c = 0; c < kColsPerThread; ++c)
-                    acc[o][c] = (t == 0) ? __fmul_rn(k[0], h[c]) : __fmaf_rn(k[t], h[c], acc[o][c]);
+                accL[o] = (t == 0) ? mul2(kk[0], hL) : fma2(kk[t], hL, accL[o]);
+                accR[o] = (t == 0) ? mul2(kk[0], hR) : fma2(kk[t], hR, accR[o]);
             }
         }
         const int o = r - kHalo;  // output row o has all five taps now
         if (o >= 0 && o < rows_valid) {
+            uint64_t vL = accL[o], vR = accR[o];
+            if (scaled) {
+                vL = mul2(vL, os2);
+                vR = mul2(vR, os2);
+            }
             float v[kColsPerThread];
-#pragma unroll
-            for (int c = 0; c < kColsPerThread; ++c) v[c] = __fmul_rn(acc[o][c], oscale);
+            unpack2(vL, v[0], v[1]);
+            unpack2(vR, v[2], v[3]);
             TOut *dst = out + static_cast<int64_t>(o) * out_pitch;
             if (vec && cols_valid == kColsPerThread) {
                 Fmt<TOut>::store4(dst, v);
@@ -160,13 +180,27 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
     }
 
     // ---------------------------------------------------------------- consumers
-    float k[kTaps];
-    float oscale = 1.f;
-    if (!BATCH) {
+    // Per-image fields in registers: once for a single image, per tile in a batch.
+    uint64_t kk[kTaps];
+    uint64_t os2 = 0;
+    bool scaled = false;
+    unsigned char *out_base = nullptr;
+    int64_t out_pitch = 0, out_plane = 0;
+    int Hv = 0, Wv = 0;
+    bool vec = false;
+    auto load_desc = [&](const ImgDesc &d) {
 #pragma unroll
-        for (int t = 0; t < kTaps; ++t) k[t] = single.k[t];
-        oscale = single.oscale;
-    }
+        for (int q = 0; q < kTaps; ++q) kk[q] = pack2(d.k[q], d.k[q]);
+        os2 = pack2(d.oscale, d.oscale);
+        scaled = d.oscale != 1.f;  // multiplying by exactly 1 would change nothing
+        out_base = static_cast<unsigned char *>(d.out);
+        out_pitch = d.out_pitch;
+        out_plane = d.out_plane;
+        Hv = d.Hv;
+        Wv = d.Wv;
+        vec = d.vec != 0;
+    };
+    if (!BATCH) load_desc(single);
     for (int64_t i = 0;; ++i) {
         const int64_t t = blockIdx.x + i * static_cast<int64_t>(gridDim.x);
         if (t >= ntiles) break;
@@ -178,23 +212,17 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             return;
         }
         const TileRec rec = info[s];
-        const ImgDesc *d = BATCH ? &descs[rec.img] : &single;
-        if (BATCH) {
-#pragma unroll
-            for (int q = 0; q < kTaps; ++q) k[q] = d->k[q];
-            oscale = d->oscale;
-        }
+        if (BATCH) load_desc(descs[rec.img]);
         const int ry0 = rec.ty * TH + warp * R;
         const int cx = rec.tx * TW + lane * kColsPerThread;
-        const int rows_valid = min(R, d->Hv - ry0);
-        const int cols_valid = min(kColsPerThread, d->Wv - cx);
+        const int rows_valid = min(R, Hv - ry0);
+        const int cols_valid = min(kColsPerThread, Wv - cx);
         if (rows_valid > 0 && cols_valid > 0) {
             const TIn *src = reinterpret_cast<const TIn *>(smem + s * STAGE) +
                              (warp * R) * BW + lane * kColsPerThread;
-            TOut *dst = reinterpret_cast<TOut *>(d->out) + rec.plane * d->out_plane +
-                        static_cast<int64_t>(ry0) * d->out_pitch + cx;
-            conv_strip<TIn, TOut, R, BW>(src, k, oscale, dst, d->out_pitch, rows_valid,
-                                         cols_valid, d->vec != 0);
+            TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
+                        static_cast<int64_t>(ry0) * out_pitch + cx;
+            conv_strip<TIn, TOut, R, BW>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);

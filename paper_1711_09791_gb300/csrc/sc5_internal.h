@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/sepconv5.h"
 
 namespace sc5 {
@@ -76,5 +78,15 @@ cudaError_t launch_empty(int n, cudaStream_t st);
 void note_launches(int64_t n);
 int dtype_bytes(int dtype);
 int num_sms();
+sc5_status fail(sc5_status st, const char *fmt, ...);
+sc5_status fail_cuda(cudaError_t e, const char *what);
+void clear_error();
+// Fused shape and CTAs/SM for a plane size (override > tuned table > default).
+sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas);
+// Shape for a set of images: tuned choice for the size class with most pixels.
+sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas);
+// Host image of a batch launch: ImgDesc[n] then (256-byte aligned) TileRec[tiles].
+sc5_status build_batch(const sc5_plan_desc &pd, int n, const sc5_image *imgs, const FusedShape &sh,
+                       std::vector<unsigned char> *blob, int64_t *ntiles, size_t *tiles_off);
 
 }  // namespace sc5

@@ -47,7 +47,8 @@ class Image(ctypes.Structure):
 
 class ServeCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_size_t), ("max_inflight", c_int32), ("dtype", c_int32),
-                ("planes", c_int32), ("n_streams", c_int32), ("max_merge", c_int32), ("merge", c_int32)]
+                ("planes", c_int32), ("n_streams", c_int32), ("max_merge", c_int32), ("merge", c_int32),
+                ("batch_window_us", c_int32)]
 
 
 class ServeStats(ctypes.Structure):
@@ -296,7 +297,7 @@ class Server:
     """Serving runtime (serve_create / serve_submit / serve_poll / serve_destroy)."""
 
     def __init__(self, hbm_budget_bytes: int, dtype="bf16", planes=3, max_inflight=64, n_streams=2,
-                 max_merge=0, merge=True):
+                 max_merge=0, merge=True, batch_window_us=0):
         cfg = ServeCfg()
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.max_inflight = max_inflight
@@ -305,6 +306,7 @@ class Server:
         cfg.n_streams = n_streams
         cfg.max_merge = max_merge
         cfg.merge = 1 if merge else 0
+        cfg.batch_window_us = batch_window_us
         h = c_void_p()
         _check(load().serve_create(byref(cfg), byref(h)), "serve_create")
         self._h = h

@@ -31,6 +31,8 @@ def test_fused_configs_listed(sc5):
                  ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]:
         cfgs = sc5.fused_configs(*pair)
         assert cfgs and all(tw == 128 and th % 32 == 0 and st >= 2 for th, tw, st in cfgs)
+        # a plan selects a shape by (tile_h, tile_w, stages): every triple must be unique
+        assert len(set(cfgs)) == len(cfgs)
     with pytest.raises(sc5.Sepconv5Error):
         sc5.fused_configs("bf16", "f16")
 
