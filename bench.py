@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip two-pass / e2e / probe / cpu legs")
+    ap.add_argument("--no-extras", action="store_true", help="only the timed fused leg")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests per offered load")
+    ap.add_argument("--legs", default="c1,c3,c4,c5", help="extra configs to run beside the headline")
     return ap.parse_args()
 
 
@@ -169,6 +171,229 @@ def oracle_sample(A: np.ndarray, k: np.ndarray, target_s: float = 10.0) -> dict:
                       f"output pixels), FP64 direct Eq. 1, one thread, {dt:.1f} s"}
 
 
+# ------------------------------------------------------------------ other configs
+
+
+def cuda_time(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def leg_c1(sc5, synth, stream):
+    """3 x 512 x 512 FP32, k = [1,4,6,4,1]/16: a latency config (L2-resident)."""
+    import torch
+    h = w = 512
+    A = torch.from_numpy(synth.image(1, h, w)).cuda()
+    out = torch.empty((P, h - 4, w - 4), dtype=torch.float32, device="cuda")
+    k = synth.kernel_binomial()
+    res = {"workload": "3x512x512 f32, k=[1,4,6,4,1]/16"}
+    for algo in ("fused", "two_pass"):
+        plan = sc5.Plan(P, h, w, w, w - 4, algo=algo)
+        ms = cuda_time(lambda: plan.run(A, out, k, stream=stream), 200, 20, stream)
+        res[f"{algo}_us"] = round(ms * 1e3, 2)
+        plan.close()
+    plan = sc5.Plan(P, h, w, w, w - 4)
+    b = sc5.Batch(plan, [{"in": A, "out": out, "H": h, "W": w, "in_pitch": w, "out_pitch": w - 4, "k": k}])
+    ms = cuda_time(lambda: b.launch(stream), 200, 20, stream)
+    res["fused_graph_us"] = round(ms * 1e3, 2)
+    b.close()
+    plan.close()
+    return res
+
+
+def _batch_images(sc5, synth, dtype, shapes, x_dev, scales):
+    """Device images of the 256-image batch in a stored format (converted on
+    the GPU from the FP32 originals: input preparation, not the method)."""
+    import torch
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}[dtype]
+    es = sc5.DTYPE_BYTES[dtype]
+    imgs, keep = [], []
+    for i, ((h, w), x) in enumerate(zip(shapes, x_dev)):
+        s = scales[i] if dtype == "fp8e4m3" else 1.0
+        pitch = -(-w * es // 16) * 16 // es
+        A = torch.zeros((P, h, pitch), dtype=tdt, device="cuda")
+        A[:, :, :w] = (x * s if s != 1.0 else x).to(tdt)
+        op = -(-(w - 4) // 4) * 4
+        imgs.append({"in": A, "H": h, "W": w, "in_pitch": pitch, "out_pitch": op,
+                     "k": synth.kernel_normalised(3000 + i), "in_scale": s, "out_scale": s})
+        keep.append(A)
+    return imgs, keep
+
+
+def _sample_errors(oracle, imgs, outs, dtype, out_dtype, m=48, seed=9):
+    """max-abs and max-relative error of sampled outputs against the FP64
+    oracle evaluated on the decoded stored inputs, one 5x5 window per pixel."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(seed))
+    max_abs, max_rel = 0.0, 0.0
+    for im, out in zip(imgs, outs):
+        h, w = im["H"], im["W"]
+        p = g.integers(0, P, m)
+        y = g.integers(0, h - 4, m)
+        x = g.integers(0, w - 4, m)
+        A = im["in"]
+        dec = A.float() / im["in_scale"] if A.dtype != torch.float32 else A
+        idx = torch.arange(5, device="cuda")
+        pt, yt, xt = (torch.from_numpy(v).cuda() for v in (p, y, x))
+        win = dec[pt[:, None, None], (yt[:, None] + idx)[:, :, None], (xt[:, None] + idx)[:, None, :]]
+        ref = oracle.direct(win.double().cpu().numpy(), np.asarray(im["k"], np.float64))[:, 0, 0]
+        got = out[pt, yt, xt]
+        got = (got.float() / im["out_scale"] if got.dtype != torch.float32 else got).double().cpu().numpy()
+        err = np.abs(got - ref)
+        max_abs = max(max_abs, float(err.max()))
+        sel = np.abs(ref) > 1.0
+        if sel.any():
+            max_rel = max(max_rel, float((err[sel] / np.abs(ref[sel])).max()))
+    return max_abs, max_rel
+
+
+def leg_batch(sc5, synth, oracle, stream, dtypes):
+    """The 256-image batch (H, W log-uniform in [64, 4096]): one persistent
+    launch over the tile work-list, replayed from a CUDA graph, shape from
+    the autotuner; FP32 and the stored formats."""
+    import torch
+    shapes = synth.batch_shapes(3, 256)
+    x_dev = [torch.from_numpy(synth.image(3000 + i, h, w)).cuda() for i, (h, w) in enumerate(shapes)]
+    scales = [448.0 / float(x.abs().max()) for x in x_dev]
+    px = sum(h * w for h, w in shapes)
+    t0 = time.perf_counter()
+    sc5.autotune(1, [(d, o) for d, o in dtypes])
+    tune_s = time.perf_counter() - t0
+    results = {"workload": f"256 images, H and W log-uniform in [64,4096] (seed 3), {px / 1e6:.1f} Mpix x 3 planes",
+               "autotune_s": round(tune_s, 1)}
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    for dtype, out_dtype in dtypes:
+        imgs, keep = _batch_images(sc5, synth, dtype, shapes, x_dev, scales)
+        odt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}[out_dtype]
+        outs = []
+        for im in imgs:
+            o = torch.empty((P, im["H"] - 4, im["out_pitch"]), dtype=odt, device="cuda")
+            im["out"] = o
+            if out_dtype == "f32":
+                im["out_scale"] = 1.0
+            outs.append(o)
+        plan = sc5.Plan(P, 64, 64, in_dtype=dtype, out_dtype=out_dtype)
+        b = sc5.Batch(plan, imgs)
+        ms = cuda_time(lambda: b.launch(stream), 20, 3, stream)
+        info = b.info()
+        alg = sum(P * h * w * sc5.DTYPE_BYTES[dtype] + P * (h - 4) * (w - 4) * sc5.DTYPE_BYTES[out_dtype]
+                  for h, w in shapes)
+        ea, er = _sample_errors(oracle, imgs, outs, dtype, out_dtype)
+        results[f"{dtype}->{out_dtype}"] = {
+            "ms": round(ms, 4), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "achieved_gbs": round(alg / ms / 1e6, 1),
+            "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4), "tiles": info["tiles"], "ctas": info["ctas"],
+            "tile": f"{info['tile_h']}x{info['tile_w']}", "max_abs_err_vs_fp64": ea, "max_rel_err_vs_fp64": er,
+            "err_sample": "48 pixels per image, FP64 oracle on the decoded stored inputs"}
+        b.close()
+        plan.close()
+        del imgs, keep, outs
+        torch.cuda.empty_cache()
+    return results
+
+
+def leg_serve(sc5, synth, n_req):
+    """Serving stream: Poisson arrivals, sizes uniform over 640x480,
+    1920x1080 and 4096x4096, per-request normalised k.  BF16 storage with
+    continuous batching against FP32 with one launch per request, at 0.5x,
+    0.8x and 0.95x of the measured saturation request rate of the BF16
+    server.  Latency = completion of the result's copy to the host minus the
+    request's scheduled arrival."""
+    import queue as _q
+    import threading as _t
+
+    import torch
+    sizes = synth.SERVE_SIZES
+    out = {"workload": f"{n_req} requests per load, sizes {sizes} (H, W), Poisson arrivals",
+           "budget_bytes": 16 << 30}
+
+    def make_pool(dtype, n_buf):
+        tdt = {"bf16": torch.int16, "f32": torch.float32}[dtype]
+        es = sc5.DTYPE_BYTES[dtype]
+        pool = []
+        for ci, (h, w) in enumerate(sizes):
+            x = synth.image(700 + ci, h, w)
+            src = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16) if dtype == "bf16" else torch.from_numpy(x)
+            src = src.contiguous().pin_memory()
+            q = _q.Queue()
+            for _ in range(n_buf):
+                q.put(torch.empty((P, h - 4, w - 4), dtype=tdt).pin_memory())
+            pool.append((src, q, h, w))
+        return pool
+
+    def run(dtype, merge, rate, n, pool, seed):
+        srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype=dtype, max_inflight=64, n_streams=2, merge=merge)
+        stream_ = synth.serve_stream(seed, n, rate) if rate else [(0.0, c, s) for (_, c, s) in synth.serve_stream(seed, n, 1.0)]
+        lat = []
+        tickets = _q.Queue()
+        px_done = [0]
+
+        def poller():
+            while True:
+                item = tickets.get()
+                if item is None:
+                    return
+                t, t_arr, t_sub, buf, q, px = item
+                l_srv = srv.poll(t, -1)
+                lat.append((t_sub + l_srv * 1e-6) - t_arr)
+                px_done[0] += px
+                q.put(buf)
+
+        th = _t.Thread(target=poller)
+        th.start()
+        t_start = time.perf_counter()
+        for (t_arr, ci, kseed) in stream_:
+            src, q, h, w = pool[ci]
+            target = t_start + t_arr
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 2e-4:
+                    time.sleep(target - now - 1e-4)
+            buf = q.get()
+            req = {"in": src, "out": buf, "H": h, "W": w, "in_pitch": w, "out_pitch": w - 4,
+                   "k": synth.kernel_normalised(kseed)}
+            t_sub = time.perf_counter()
+            tk = srv.submit(req)
+            while tk is None:
+                time.sleep(1e-4)
+                tk = srv.submit(req)
+            tickets.put((tk, target, t_sub, buf, q, h * w))
+        tickets.put(None)
+        th.join()
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        lat_ms = np.array(lat) * 1e3
+        return {"offered_req_s": round(rate, 1) if rate else None, "achieved_req_s": round(n / wall, 1),
+                "mpix_s": round(px_done[0] / wall / 1e6, 1), "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3), "launches": st["launches"],
+                "merged_max": st["merged_max"], "resident_peak_bytes": st["resident_peak_bytes"]}
+
+    pool_bf = make_pool("bf16", 24)
+    sat = run("bf16", True, 0.0, min(n_req, 2000), pool_bf, 11)
+    rate_sat = sat["achieved_req_s"]
+    out["saturation_bf16_merged"] = sat
+    pool_f32 = make_pool("f32", 24)
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * rate_sat
+        out[f"load_{frac}"] = {"bf16_merged": run("bf16", True, rate, n_req, pool_bf, 20 + int(frac * 100)),
+                               "f32_per_request": run("f32", False, rate, n_req, pool_f32, 20 + int(frac * 100))}
+    del pool_bf, pool_f32
+    return out
+
+
 # ------------------------------------------------------------------ main legs
 
 
@@ -276,6 +501,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = oracle_sample(A, k)
     plan.close()
+    del A_host, out_host
+    legs = [] if args.no_extras or rank != 0 else [x.strip() for x in args.legs.split(",") if x.strip()]
+    if legs:
+        import oracle
+        del A_dev, out
+        torch.cuda.empty_cache()
+        if "c1" in legs:
+            extras["small_c1"] = leg_c1(sepconv5, synth, stream)
+        if "c3" in legs or "c4" in legs:
+            pairs = [("f32", "f32")] if "c3" in legs else []
+            if "c4" in legs:
+                pairs += [("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
+                          ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
+            extras["batch_c3_c4"] = leg_batch(sepconv5, synth, oracle, stream, pairs)
+        if "c5" in legs:
+            extras["serve_c5"] = leg_serve(sepconv5, synth, args.serve_requests)
     if rank != 0:
         return None
     line = {
