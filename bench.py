@@ -37,7 +37,8 @@ SEED = 2
 WORKLOAD = "3x8192x8192 f32 fused single-pass, k = 5 seeded uniform(0,1) taps / sum"
 METRIC = "3-plane Mpix/s (fused single-pass, 3x8192x8192 FP32)"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fused_f32_3x8192x8192.md")
-FUSED_SOURCES = ["sc5_fused_impl.cuh", "sc5_device.cuh", "sc5_fused_f32.cu", "sc5_fused.cu"]
+# the files that define the fused kernel's code (template, device helpers, FP32 shapes)
+FUSED_SOURCES = ["sc5_fused_impl.cuh", "sc5_device.cuh", "sc5_fused_f32.cu"]
 
 
 def parse():
@@ -53,6 +54,27 @@ def parse():
 
 
 # ------------------------------------------------------------------ helpers
+
+
+def rank_image_seed(rank: int) -> int:
+    """Every rank convolves its own image (weak scaling, no data exchange)."""
+    return SEED + rank
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a per-rank time over all ranks (a no-op on one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, pixels_per_rank: int, ms_per_step: float) -> float:
+    """3-plane Mpix/s of the whole job: all ranks' pixels over the slowest rank's time."""
+    return world * pixels_per_rank / (ms_per_step / 1e3) / 1e6
 
 
 def algorithmic_bytes(h: int, w: int, planes: int = P, es_in: int = 4, es_out: int = 4) -> int:
@@ -169,6 +191,40 @@ def oracle_sample(A: np.ndarray, k: np.ndarray, target_s: float = 10.0) -> dict:
     return {"value": px / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
             "sample": f"top {rows + 4} input rows x {W} cols x {P} planes of the image ({rows} x {W - 4} "
                       f"output pixels), FP64 direct Eq. 1, one thread, {dt:.1f} s"}
+
+
+def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
+    """Copy-only times for the offload bytes: host->device alone,
+    device->host alone, and both at once on two streams."""
+    import torch
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def t(fn, reps=5):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3 / reps
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            A_dev.copy_(A_host, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            out_host.copy_(out_dev, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    th, td, tb = t(h2d), t(d2h), t(both)
+    nb_in, nb_out = A_host.numel() * 4, out_host.numel() * 4
+    return {"h2d_ms": round(th, 4), "d2h_ms": round(td, 4), "both_ms": round(tb, 4),
+            "h2d_gbs": round(nb_in / th / 1e6, 1), "d2h_gbs": round(nb_out / td / 1e6, 1),
+            "both_gbs": round((nb_in + nb_out) / tb / 1e6, 1)}
 
 
 # ------------------------------------------------------------------ other configs
@@ -405,7 +461,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     sepconv5.load()
-    A = synth.image(SEED + rank, H, W)
+    A = synth.image(rank_image_seed(rank), H, W)
     k = synth.kernel_normalised(SEED)
     A_dev = torch.from_numpy(A).to(dev)
     out = torch.empty((P, H - 4, W - 4), dtype=torch.float32, device=dev)
@@ -418,12 +474,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, dev)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -454,7 +505,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     alg = algorithmic_bytes(H, W)
     pixels = H * W
-    value = world * pixels / (ms / 1e3) / 1e6
+    value = whole_job_value(world, pixels, ms)
     peaks = measured_peaks()
     if peaks and peaks.get("hbm_gbs"):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
@@ -497,6 +548,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
            "h2d_bytes_per_step": P * H * W * 4, "d2h_bytes_per_step": P * (H - 4) * (W - 4) * 4,
            "ms_per_step": round(e2e_ms, 4), "launches_per_step": e2e_launches,
            "api": "sepconv5_run_host (pinned host buffers, band-pipelined copies)"}
+    # the ceiling of the offload path: plain copies over the CPU-GPU link
+    e2e["link"] = copy_probe(A_host, out_host, A_dev, out, dev)
+    lb = e2e["link"]
+    e2e["frac_of_link"] = round(max(lb["h2d_ms"], lb["d2h_ms"], lb["both_ms"]) / e2e_ms, 4)
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = oracle_sample(A, k)

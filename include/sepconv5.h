@@ -306,6 +306,14 @@ SC5_API const char *sepconv5_last_error(void);
  * counterpart of the paper's empty-kernel measurement in Sec. 6). */
 SC5_API sc5_status sepconv5_empty_launches(int32_t n, void *stream);
 
+/* Failure-path self-test: launch one warp that waits, with the same bounded
+ * mbarrier wait the fused kernels use, on a barrier that nothing completes.
+ * After limit_us (1..100000) of GPU time it writes error code 1 into the
+ * device status word and exits normally -- no trap, no fault; the context
+ * stays usable.  A following sepconv5_device_status then reports SC5_EDEVICE
+ * with code 1 (and clears it). */
+SC5_API sc5_status sepconv5_selftest_wait_timeout(int32_t limit_us, void *stream);
+
 /* Number of kernels this library launched in this process (all entry points). */
 SC5_API int64_t sepconv5_launch_count(void);
 

@@ -760,3 +760,11 @@ extern "C" sc5_status sepconv5_empty_launches(int32_t n, void *stream)
 }
 
 extern "C" int64_t sepconv5_launch_count(void) { return g_launches.load(); }
+
+extern "C" sc5_status sepconv5_selftest_wait_timeout(int32_t limit_us, void *stream)
+{
+    clear_error();
+    if (limit_us < 1 || limit_us > 100000) return fail(SC5_EINVAL, "limit_us must be in [1, 100000]");
+    cudaError_t e = launch_wait_selftest(limit_us, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "self-test launch");
+}

@@ -154,6 +154,31 @@ cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDe
     return err;
 }
 
+// One warp waits, with the kernels' bounded wait, on a fresh barrier that
+// nothing will ever complete; when the limit runs out it records the time-out
+// code in the status word and returns.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!ok && threadIdx.x == 0) record_error(status, kDevErrTmaTimeout);
+}
+
+cudaError_t launch_wait_selftest(int limit_us, cudaStream_t st)
+{
+    int *status = status_ptr();
+    if (!status) return cudaErrorInvalidDevicePointer;
+    wait_selftest_kernel<<<1, 32, 0, st>>>(static_cast<uint64_t>(limit_us) * 1000ull, status);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) note_launches(1);
+    return err;
+}
+
 cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code)
 {
     int *p = status_ptr();

@@ -62,6 +62,7 @@ cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgD
 cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDesc *descs,
                                const TileRec *tiles, int64_t ntiles, int grid, cudaStream_t st);
 cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code);
+cudaError_t launch_wait_selftest(int limit_us, cudaStream_t st);
 
 // Two-pass kernels and helpers (sc5_twopass.cu).
 cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,

@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "serve_get_stats": [V, POINTER(ServeStats)],
         "serve_destroy": [V],
         "sepconv5_empty_launches": [c_int32, V],
+        "sepconv5_selftest_wait_timeout": [c_int32, V],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -287,6 +288,10 @@ def tune_lookup(in_dtype, out_dtype, H, W) -> tuple[dict, bool]:
 
 def empty_launches(n: int, stream=None):
     _check(load().sepconv5_empty_launches(n, _stream(stream)), "sepconv5_empty_launches")
+
+
+def selftest_wait_timeout(limit_us: int, stream=None):
+    _check(load().sepconv5_selftest_wait_timeout(limit_us, _stream(stream)), "sepconv5_selftest_wait_timeout")
 
 
 def launch_count() -> int:

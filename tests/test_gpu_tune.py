@@ -1,0 +1,46 @@
+"""The autotuner: a quick tuning pass fills one entry per size class, the
+table round-trips through its JSON file, and plans pick the tuned shape."""
+import json
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_table_roundtrip(tmp_path):
+    import torch
+    from paper_1711_09791_gb300 import sepconv5 as sc5
+    sc5.load()
+    path = str(tmp_path / "tune.json")
+    sc5.autotune(1, [("f32", "f32"), ("bf16", "bf16")], path)
+    table = json.load(open(path))
+    assert table["gpu"] == torch.cuda.get_device_name(0)
+    assert len(table["entries"]) == 2 * 7
+    compiled = {p: set(sc5.fused_configs(*p)) for p in [("f32", "f32"), ("bf16", "bf16")]}
+    for e in table["entries"]:
+        pair = ({0: "f32", 1: "bf16"}[e["in"]], {0: "f32", 1: "bf16"}[e["out"]])
+        assert (e["tile_h"], e["tile_w"], e["stages"]) in compiled[pair]
+        assert e["ctas"] >= 1 and e["us"] > 0
+    cfg, found = sc5.tune_lookup("f32", "f32", 8192, 8192)
+    assert found
+    sc5.autotune(0, [])  # clear
+    assert not sc5.tune_lookup("f32", "f32", 8192, 8192)[1]
+    sc5.tune_load(path)
+    cfg2, found2 = sc5.tune_lookup("f32", "f32", 8192, 8192)
+    assert found2 and cfg2 == cfg
+    # a batch of large images takes the tuned shape of their size class
+    A = torch.zeros((3, 3000, 3000), dtype=torch.float32, device="cuda")
+    out = torch.zeros((3, 2996, 2996), dtype=torch.float32, device="cuda")
+    plan = sc5.Plan(3, 64, 64)
+    b = sc5.Batch(plan, [{"in": A, "out": out, "H": 3000, "W": 3000, "in_pitch": 3000, "out_pitch": 2996,
+                          "k": [0, 0, 1, 0, 0]}])
+    want, _ = sc5.tune_lookup("f32", "f32", 2048, 4096)  # the dominant class of one 3000^2 image
+    info = b.info()
+    assert (info["tile_h"], info["tile_w"]) == (want["tile_h"], want["tile_w"])
+    b.launch()
+    torch.cuda.synchronize()
+    assert sc5.device_status() == 0
+    b.close()
+    plan.close()
+    sc5.autotune(0, [])
