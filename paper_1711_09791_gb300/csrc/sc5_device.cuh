@@ -150,10 +150,19 @@ __device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float lo, float hi)
 
 // Storage traits.  load8 reads stored elements p[0..7] (p aligned to 4
 // elements) and widens them exactly to float.  store4 narrows 4 floats.
+
+// Pairings of the 8 widened inputs a0..a7 for the packed row pass:
+//   adjacent  E = (a0,a1), (a2,a3), (a4,a5), (a6,a7) and shifted O = (a1,a2),
+//             (a3,a4), (a5,a6) -- free for FP32 data, whose 16-byte loads
+//             already fill register pairs;
+//   stride 2  S_j = (a_j, a_{j+2}), j = 0..5 -- for narrow formats, where every
+//             element is widened by one instruction anyway and can be widened
+//             straight into its slot of a pair.
 template <class T> struct Fmt;
 
 template <> struct Fmt<float> {
     static constexpr int bytes = 4;
+    static constexpr bool kStride2 = false;
     __device__ static __forceinline__ void load8(const float *p, float (&a)[8])
     {
         const float4 u = *reinterpret_cast<const float4 *>(p);
@@ -171,6 +180,7 @@ template <> struct Fmt<float> {
 
 template <> struct Fmt<bf16_t> {
     static constexpr int bytes = 2;
+    static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const bf16_t *p, float (&a)[8])
     {
         // a bfloat16 is the upper half of a binary32: one shift or mask per element
@@ -197,6 +207,7 @@ template <> struct Fmt<bf16_t> {
 
 template <> struct Fmt<f16_t> {
     static constexpr int bytes = 2;
+    static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const f16_t *p, float (&a)[8])
     {
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
@@ -227,6 +238,7 @@ template <> struct Fmt<f16_t> {
 
 template <> struct Fmt<fp8e4m3_t> {
     static constexpr int bytes = 1;
+    static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const fp8e4m3_t *p, float (&a)[8])
     {
         const uint32_t u = *reinterpret_cast<const uint32_t *>(p);

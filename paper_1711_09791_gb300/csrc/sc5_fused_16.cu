@@ -10,7 +10,10 @@ namespace sc5 {
         make_entry<TI, TO, 128, 128, 8, 4>(),                   \
         make_entry<TI, TO, 64, 128, 4, 4>(),                    \
         make_entry<TI, TO, 32, 128, 2, 8>(),                    \
-        make_entry<TI, TO, 128, 128, 8, 3>(),                   \
+        make_entry<TI, TO, 120, 128, 4, 4>(),                   \
+        make_entry<TI, TO, 240, 128, 8, 3>(),                   \
+        make_entry<TI, TO, 128, 128, 16, 3>(),                  \
+        make_entry<TI, TO, 128, 128, 16, 2>(),                  \
     }
 
 int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
@@ -19,10 +22,10 @@ int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
     static const FusedEntry bf_f32[] = SC5_SHAPES_16(bf16_t, float);
     static const FusedEntry h_h[] = SC5_SHAPES_16(f16_t, f16_t);
     static const FusedEntry h_f32[] = SC5_SHAPES_16(f16_t, float);
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) { *out = bf_bf; return 5; }
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) { *out = bf_f32; return 5; }
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) { *out = h_h; return 5; }
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) { *out = h_f32; return 5; }
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) { *out = bf_bf; return static_cast<int>(sizeof bf_bf / sizeof bf_bf[0]); }
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) { *out = bf_f32; return static_cast<int>(sizeof bf_f32 / sizeof bf_f32[0]); }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) { *out = h_h; return static_cast<int>(sizeof h_h / sizeof h_h[0]); }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) { *out = h_f32; return static_cast<int>(sizeof h_f32 / sizeof h_f32[0]); }
     return 0;
 }
 

@@ -14,6 +14,7 @@ int fused_entries_f32(int out_dtype, const FusedEntry **out)
         make_entry<float, float, 32, 128, 4, 2>(),
         make_entry<float, float, 32, 128, 2, 4>(),
         make_entry<float, float, 32, 128, 4, 5>(),
+        make_entry<float, float, 120, 128, 4, 3>(),  // 30 consumer warps
     };
     if (out_dtype == SC5_F32) { *out = f32_f32; return static_cast<int>(sizeof f32_f32 / sizeof f32_f32[0]); }
     return 0;

@@ -47,34 +47,51 @@ __host__ __device__ constexpr int fused_stage_bytes()
 //   s:   shared memory at (first input row of the strip, first input column)
 //   out: global memory at (first output row, first output column)
 //   kk:  the taps as pairs (k[t], k[t]); os2 = (oscale, oscale)
-// Columns are processed as two pairs, (0,1) and (2,3), with packed FP32
-// arithmetic.  For column pair (c, c+1), tap t multiplies the input pair
-// (a[c+t], a[c+t+1]): even t gives the aligned pairs E = (a0,a1), (a2,a3), ...,
-// odd t the shifted pairs O = (a1,a2), (a3,a4), (a5,a6).  Per element this is
-// exactly hdot's sequence: k0*a0, then fused multiply-adds for t = 1..4.
+// Columns are processed as two pairs with packed FP32 arithmetic.  FP32 data
+// use column pairs (0,1) and (2,3): tap t multiplies the input pair
+// (a[c+t], a[c+t+1]), even t the aligned pairs E, odd t the shifted pairs O.
+// Narrow formats use column pairs (0,2) and (1,3): tap t multiplies the
+// stride-2 pair (a[c+t], a[c+t+2]).  Per element this is exactly hdot's
+// sequence: k0*a0, then fused multiply-adds for t = 1..4.
 template <class TIn, class TOut, int R, int BW>
 __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps],
                                            uint64_t os2, bool scaled, TOut *__restrict__ out,
                                            int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
 {
+    // accumulator pairs: columns (0,1) and (2,3), or (0,2) and (1,3) for stride-2 pairing
     uint64_t accL[R], accR[R];
 #pragma unroll
     for (int r = 0; r < R + kHalo; ++r) {
         float a[8];
         Fmt<TIn>::load8(s + r * BW, a);
-        const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
-        const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
-        const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
-        uint64_t hL = mul2(kk[0], E0);
-        hL = fma2(kk[1], O0, hL);
-        hL = fma2(kk[2], E1, hL);
-        hL = fma2(kk[3], O1, hL);
-        hL = fma2(kk[4], E2, hL);
-        uint64_t hR = mul2(kk[0], E1);
-        hR = fma2(kk[1], O1, hR);
-        hR = fma2(kk[2], E2, hR);
-        hR = fma2(kk[3], O2, hR);
-        hR = fma2(kk[4], E3, hR);
+        uint64_t hL, hR;
+        if constexpr (Fmt<TIn>::kStride2) {
+            uint64_t S[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) S[j] = pack2(a[j], a[j + 2]);
+            // (h0, h2) = sum_t k[t] (a[t], a[t+2]);  (h1, h3) = sum_t k[t] (a[t+1], a[t+3])
+            hL = mul2(kk[0], S[0]);
+            hR = mul2(kk[0], S[1]);
+#pragma unroll
+            for (int t = 1; t < kTaps; ++t) {
+                hL = fma2(kk[t], S[t], hL);
+                hR = fma2(kk[t], S[t + 1], hR);
+            }
+        } else {
+            const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
+            const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
+            const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
+            hL = mul2(kk[0], E0);
+            hL = fma2(kk[1], O0, hL);
+            hL = fma2(kk[2], E1, hL);
+            hL = fma2(kk[3], O1, hL);
+            hL = fma2(kk[4], E2, hL);
+            hR = mul2(kk[0], E1);
+            hR = fma2(kk[1], O1, hR);
+            hR = fma2(kk[2], E2, hR);
+            hR = fma2(kk[3], O2, hR);
+            hR = fma2(kk[4], E3, hR);
+        }
         // input row r carries tap t = r - o of output row o
 #pragma unroll
         for (int t = 0; t < kTaps; ++t) {
@@ -92,8 +109,13 @@ __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint
                 vR = mul2(vR, os2);
             }
             float v[kColsPerThread];
-            unpack2(vL, v[0], v[1]);
-            unpack2(vR, v[2], v[3]);
+            if constexpr (Fmt<TIn>::kStride2) {
+                unpack2(vL, v[0], v[2]);
+                unpack2(vR, v[1], v[3]);
+            } else {
+                unpack2(vL, v[0], v[1]);
+                unpack2(vR, v[2], v[3]);
+            }
             TOut *dst = out + static_cast<int64_t>(o) * out_pitch;
             if (vec && cols_valid == kColsPerThread) {
                 Fmt<TOut>::store4(dst, v);
