@@ -90,8 +90,11 @@ typedef enum {
 } sc5_border;
 
 typedef enum {
-    SC5_ALGO_FUSED = 0,
-    SC5_ALGO_TWO_PASS = 1
+    SC5_ALGO_FUSED = 0,     /* single pass, separable arithmetic (10 FMA per output) */
+    SC5_ALGO_TWO_PASS = 1,  /* horizontal pass to an FP32 intermediate in HBM, then vertical pass */
+    SC5_ALGO_DIRECT = 2     /* single pass, direct form: 25 products per output with the 5x5
+                               matrix K (Eq. 1 / Eq. 3); sepconv5_run uses K = k k^T rounded to
+                               FP32, sepconv5_run_K takes any K */
 } sc5_algo;
 
 /* Plan descriptor.  Pitches are in elements of the respective dtype.
@@ -141,6 +144,14 @@ SC5_API sc5_status sepconv5_plan_destroy(sc5_plan plan);
  * `out` must not overlap.  Asynchronous on `stream`. */
 SC5_API sc5_status sepconv5_run(sc5_plan plan, const void *in, void *out, const float k[5],
                         float in_scale, float out_scale, void *stream);
+
+/* Direct single-pass form with a general (not necessarily separable) 5x5
+ * matrix: B[p][y][x] = sum_i sum_j A[p][y+i-2][x+j-2] * K[i*5+j] (Eq. 1, the
+ * "general algorithm" of Sec. 5.1), summed in FP32 in the row-major order of
+ * Eq. 3.  K: host array of 25 finite floats, row-major, copied by value.  The
+ * plan must have algo SC5_ALGO_DIRECT; other arguments as for sepconv5_run. */
+SC5_API sc5_status sepconv5_run_K(sc5_plan plan, const void *in, void *out, const float K[25],
+                                  float in_scale, float out_scale, void *stream);
 
 /* Offload form (the co-processor model of Sec. 7: copy the image to the
  * device, convolve, copy the result back): host_in and host_out are HOST

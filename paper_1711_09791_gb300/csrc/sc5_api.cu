@@ -158,7 +158,8 @@ static bool taps_finite(const float *k)
 // Fill an ImgDesc for one image (tensor map included).
 static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border, const FusedShape &sh,
                             const void *in, void *out, int P, int H, int W, int64_t in_pitch,
-                            int64_t out_pitch, const float *k, float in_scale, float out_scale)
+                            int64_t out_pitch, const float *k, float in_scale, float out_scale,
+                            const float *K = nullptr)
 {
     std::memset(d, 0, sizeof *d);
     sc5_status st = encode_image_map(&d->tmap, in_dtype, in, P, H, W, in_pitch,
@@ -179,6 +180,8 @@ static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border,
     d->tiles_x = (d->Wv + sh.tile_w - 1) / sh.tile_w;
     d->tiles_y = (d->Hv + sh.tile_h - 1) / sh.tile_h;
     for (int i = 0; i < kTaps; ++i) d->k[i] = k[i];
+    for (int i = 0; i < kTaps * kTaps; ++i)
+        d->K[i] = K ? K[i] : static_cast<float>(static_cast<double>(k[i / kTaps]) * k[i % kTaps]);
     d->oscale = static_cast<float>(static_cast<double>(out_scale) / static_cast<double>(in_scale));
     d->vec = (reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && out_pitch % 4 == 0) ? 1 : 0;
     return SC5_OK;
@@ -213,15 +216,19 @@ struct sc5_plan_s {
 };
 
 namespace sc5 {
-sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas)
+sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
+                        bool direct)
 {
     if (ov && (ov->tile_h || ov->tile_w || ov->stages)) {
         const int i = fused_find_shape(in_dtype, out_dtype, ov->tile_h ? ov->tile_h : 64,
-                                       ov->tile_w ? ov->tile_w : 128, ov->stages);
+                                       ov->tile_w ? ov->tile_w : 128, ov->stages, direct);
         if (i < 0) return fail(SC5_EINVAL, "no compiled fused shape %dx%d with %d stages for this dtype pair",
                                ov->tile_h, ov->tile_w, ov->stages);
         *idx = i;
         *ctas = ov->ctas_per_sm;
+    } else if (direct) {
+        *idx = 0;
+        if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
     } else {
         int th, tw, stg, c;
         if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &stg, &c)) {
@@ -231,7 +238,7 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         if (*idx < 0) *idx = 0;
         if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
     }
-    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx);
+    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx, direct);
     if (maxc <= 0) return fail(SC5_ECUDA, "occupancy query failed for fused shape %d", *idx);
     if (*ctas <= 0 || *ctas > maxc) *ctas = maxc;
     return SC5_OK;
@@ -244,7 +251,8 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     if (!desc || !out) return fail(SC5_EINVAL, "null argument");
     *out = nullptr;
     const sc5_plan_desc &d = *desc;
-    if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS) return fail(SC5_EINVAL, "unknown algo %d", d.algo);
+    if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS && d.algo != SC5_ALGO_DIRECT)
+        return fail(SC5_EINVAL, "unknown algo %d", d.algo);
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
                                 d.in_pitch, d.out_pitch, 1.f, 1.f, false);
     if (st != SC5_OK) return st;
@@ -256,12 +264,13 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     if (!p) return fail(SC5_ENOMEM, "host allocation failed");
     p->d = d;
     cudaGetDevice(&p->device);
-    st = choose_shape(d.in_dtype, d.out_dtype, d.H, d.W, &d, &p->shape_idx, &p->ctas_per_sm);
+    const bool direct = d.algo == SC5_ALGO_DIRECT;
+    st = choose_shape(d.in_dtype, d.out_dtype, d.H, d.W, &d, &p->shape_idx, &p->ctas_per_sm, direct);
     if (st != SC5_OK) {
         delete p;
         return st;
     }
-    fused_shape(d.in_dtype, d.out_dtype, p->shape_idx, &p->shape);
+    fused_shape(d.in_dtype, d.out_dtype, p->shape_idx, &p->shape, direct);
     if (d.algo == SC5_ALGO_TWO_PASS) {
         p->t_pitch = (static_cast<int64_t>(d.W - kHalo) + 3) / 4 * 4;
         const size_t bytes = static_cast<size_t>(d.planes) * d.H * p->t_pitch * sizeof(float);
@@ -331,6 +340,23 @@ static sc5_status run_frame(const sc5_plan_desc &d, const void *in, void *out, f
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "frame launch");
 }
 
+// One launch of the fused (separable) or direct single-pass kernel over the image.
+static sc5_status run_single_pass(sc5_plan p, const void *in, void *out, const float *k, const float *K,
+                                  float in_scale, float out_scale, cudaStream_t s)
+{
+    const sc5_plan_desc &d = p->d;
+    ImgDesc desc;
+    sc5_status st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, in, out, d.planes, d.H, d.W,
+                              d.in_pitch, d.out_pitch, k, in_scale, out_scale, K);
+    if (st != SC5_OK) return st;
+    const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
+    cudaError_t e = launch_fused_single(d.in_dtype, d.out_dtype, p->shape_idx, desc, ntiles, grid, s,
+                                        d.algo == SC5_ALGO_DIRECT);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "single-pass launch");
+}
+
 extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const float k[5],
                                    float in_scale, float out_scale, void *stream)
 {
@@ -345,16 +371,27 @@ extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const 
     if (d.algo == SC5_ALGO_TWO_PASS) {
         st = run_two_pass(p, in, out, k, in_scale, out_scale, s);
     } else {
-        ImgDesc desc;
-        st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, in, out, d.planes, d.H, d.W,
-                       d.in_pitch, d.out_pitch, k, in_scale, out_scale);
-        if (st != SC5_OK) return st;
-        const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
-        const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
-        const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
-        cudaError_t e = launch_fused_single(d.in_dtype, d.out_dtype, p->shape_idx, desc, ntiles, grid, s);
-        if (e != cudaSuccess) return fail_cuda(e, "fused launch");
+        st = run_single_pass(p, in, out, k, nullptr, in_scale, out_scale, s);
     }
+    if (st != SC5_OK) return st;
+    return run_frame(d, in, out, in_scale, out_scale, s);
+}
+
+extern "C" sc5_status sepconv5_run_K(sc5_plan p, const void *in, void *out, const float K[25], float in_scale,
+                                     float out_scale, void *stream)
+{
+    clear_error();
+    if (!p || !K) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    if (d.algo != SC5_ALGO_DIRECT) return fail(SC5_EINVAL, "sepconv5_run_K needs a plan with algo SC5_ALGO_DIRECT");
+    sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
+                                d.out_pitch, in_scale, out_scale, true);
+    if (st != SC5_OK) return st;
+    for (int i = 0; i < kTaps * kTaps; ++i)
+        if (!std::isfinite(K[i])) return fail(SC5_EINVAL, "K must be finite");
+    const float zero_k[kTaps] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    st = run_single_pass(p, in, out, zero_k, K, in_scale, out_scale, s);
     if (st != SC5_OK) return st;
     return run_frame(d, in, out, in_scale, out_scale, s);
 }

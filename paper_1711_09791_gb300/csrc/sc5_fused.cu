@@ -11,41 +11,45 @@ namespace sc5 {
 int fused_entries_f32(int out_dtype, const FusedEntry **out);
 int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out);
 int fused_entries_fp8(int out_dtype, const FusedEntry **out);
+int fused_direct_entries_f32(int out_dtype, const FusedEntry **out);
+int fused_direct_entries_16(int in_dtype, int out_dtype, const FusedEntry **out);
+int fused_direct_entries_fp8(int out_dtype, const FusedEntry **out);
 
 // Device status word: 0 = no error; a kernel whose bounded wait ran out
 // writes its error code here (first writer wins).
 __device__ int g_status;
 
-static int entries(int in_dtype, int out_dtype, const FusedEntry **e)
+static int entries(int in_dtype, int out_dtype, const FusedEntry **e, bool direct = false)
 {
     switch (in_dtype) {
-    case SC5_F32: return fused_entries_f32(out_dtype, e);
+    case SC5_F32: return direct ? fused_direct_entries_f32(out_dtype, e) : fused_entries_f32(out_dtype, e);
     case SC5_BF16:
-    case SC5_F16: return fused_entries_16(in_dtype, out_dtype, e);
-    case SC5_FP8E4M3: return fused_entries_fp8(out_dtype, e);
+    case SC5_F16:
+        return direct ? fused_direct_entries_16(in_dtype, out_dtype, e) : fused_entries_16(in_dtype, out_dtype, e);
+    case SC5_FP8E4M3: return direct ? fused_direct_entries_fp8(out_dtype, e) : fused_entries_fp8(out_dtype, e);
     default: return 0;
     }
 }
 
-int fused_num_shapes(int in_dtype, int out_dtype)
+int fused_num_shapes(int in_dtype, int out_dtype, bool direct)
 {
     const FusedEntry *e;
-    return entries(in_dtype, out_dtype, &e);
+    return entries(in_dtype, out_dtype, &e, direct);
 }
 
-bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s)
+bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e);
+    const int n = entries(in_dtype, out_dtype, &e, direct);
     if (idx < 0 || idx >= n) return false;
     *s = e[idx].shape;
     return true;
 }
 
-int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages)
+int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e);
+    const int n = entries(in_dtype, out_dtype, &e, direct);
     for (int i = 0; i < n; ++i)
         if (e[i].shape.tile_h == tile_h && e[i].shape.tile_w == tile_w &&
             (stages == 0 || e[i].shape.stages == stages))
@@ -93,10 +97,10 @@ static int *status_ptr()
     return ptrs[dev];
 }
 
-int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx)
+int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e);
+    const int n = entries(in_dtype, out_dtype, &e, direct);
     if (idx < 0 || idx >= n) return -1;
     if (prepare_fn(e[idx].single_fn, e[idx].smem) != cudaSuccess) return -1;
     int blocks = 0;
@@ -106,10 +110,10 @@ int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx)
     return blocks;
 }
 
-cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx)
+cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e);
+    const int n = entries(in_dtype, out_dtype, &e, direct);
     if (idx < 0 || idx >= n) return cudaErrorInvalidValue;
     cudaError_t err = prepare_fn(e[idx].single_fn, e[idx].smem);
     if (err == cudaSuccess) err = prepare_fn(e[idx].batch_fn, e[idx].smem);
@@ -118,13 +122,13 @@ cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx)
 }
 
 cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgDesc &d,
-                                int64_t ntiles, int grid, cudaStream_t st)
+                                int64_t ntiles, int grid, cudaStream_t st, bool direct)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e);
+    const int n = entries(in_dtype, out_dtype, &e, direct);
     if (idx < 0 || idx >= n || grid < 1) return cudaErrorInvalidValue;
     if (ntiles <= 0) return cudaSuccess;
-    cudaError_t err = fused_prepare(in_dtype, out_dtype, idx);
+    cudaError_t err = fused_prepare(in_dtype, out_dtype, idx, direct);
     if (err != cudaSuccess) return err;
     int *status = status_ptr();
     const ImgDesc *no_descs = nullptr;

@@ -29,4 +29,23 @@ int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
     return 0;
 }
 
+#define SC5_DIRECT_16(TI, TO)                                   \
+    {                                                           \
+        make_entry<TI, TO, 64, 128, 4, 4, true>(),              \
+        make_entry<TI, TO, 128, 128, 8, 3, true>(),             \
+    }
+
+int fused_direct_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)
+{
+    static const FusedEntry bf_bf[] = SC5_DIRECT_16(bf16_t, bf16_t);
+    static const FusedEntry bf_f32[] = SC5_DIRECT_16(bf16_t, float);
+    static const FusedEntry h_h[] = SC5_DIRECT_16(f16_t, f16_t);
+    static const FusedEntry h_f32[] = SC5_DIRECT_16(f16_t, float);
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) { *out = bf_bf; return 2; }
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) { *out = bf_f32; return 2; }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) { *out = h_h; return 2; }
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) { *out = h_f32; return 2; }
+    return 0;
+}
+
 }  // namespace sc5

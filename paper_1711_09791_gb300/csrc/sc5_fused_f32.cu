@@ -20,4 +20,14 @@ int fused_entries_f32(int out_dtype, const FusedEntry **out)
     return 0;
 }
 
+int fused_direct_entries_f32(int out_dtype, const FusedEntry **out)
+{
+    static const FusedEntry f32_f32[] = {
+        make_entry<float, float, 64, 128, 4, 3, true>(),
+        make_entry<float, float, 32, 128, 2, 4, true>(),
+    };
+    if (out_dtype == SC5_F32) { *out = f32_f32; return static_cast<int>(sizeof f32_f32 / sizeof f32_f32[0]); }
+    return 0;
+}
+
 }  // namespace sc5

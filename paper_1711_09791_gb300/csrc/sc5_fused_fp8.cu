@@ -26,4 +26,19 @@ int fused_entries_fp8(int out_dtype, const FusedEntry **out)
     return 0;
 }
 
+int fused_direct_entries_fp8(int out_dtype, const FusedEntry **out)
+{
+    static const FusedEntry e_e[] = {
+        make_entry<fp8e4m3_t, fp8e4m3_t, 64, 128, 4, 4, true>(),
+        make_entry<fp8e4m3_t, fp8e4m3_t, 128, 128, 8, 3, true>(),
+    };
+    static const FusedEntry e_f32[] = {
+        make_entry<fp8e4m3_t, float, 64, 128, 4, 4, true>(),
+        make_entry<fp8e4m3_t, float, 128, 128, 8, 3, true>(),
+    };
+    if (out_dtype == SC5_FP8E4M3) { *out = e_e; return 2; }
+    if (out_dtype == SC5_F32) { *out = e_f32; return 2; }
+    return 0;
+}
+
 }  // namespace sc5

@@ -43,54 +43,84 @@ __host__ __device__ constexpr int fused_stage_bytes()
     return (fused_box_w<TIn>(TW) * (TH + kHalo) * Fmt<TIn>::bytes + 127) / 128 * 128;
 }
 
-// One lane's strip: R output rows x 4 output columns.
+// The input pairs of one row for the packed arithmetic.  Output columns are
+// processed as two pairs, L and R; tap j of the row pass multiplies PL[j] into
+// L and PR[j] into R.  FP32 data use column pairs (0,1) and (2,3): PL[j] =
+// (a[j], a[j+1]), PR[j] = (a[j+2], a[j+3]) -- even j are the register pairs the
+// 16-byte loads already fill, odd j the shifted pairs.  Narrow formats use
+// column pairs (0,2) and (1,3): PL[j] = (a[j], a[j+2]), PR[j] = (a[j+1], a[j+3]),
+// each half widened straight into its slot.
+template <class TIn>
+__device__ __forceinline__ void row_pairs(const TIn *__restrict__ p, uint64_t (&PL)[kTaps], uint64_t (&PR)[kTaps])
+{
+    float a[8];
+    Fmt<TIn>::load8(p, a);
+    if constexpr (Fmt<TIn>::kStride2) {
+        uint64_t S[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) S[j] = pack2(a[j], a[j + 2]);
+#pragma unroll
+        for (int j = 0; j < kTaps; ++j) {
+            PL[j] = S[j];
+            PR[j] = S[j + 1];
+        }
+    } else {
+        const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
+        const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
+        const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
+        PL[0] = E0; PL[1] = O0; PL[2] = E1; PL[3] = O1; PL[4] = E2;
+        PR[0] = E1; PR[1] = O1; PR[2] = E2; PR[3] = O2; PR[4] = E3;
+    }
+}
+
+// Store output row o of a strip: scale (unless 1), unpair, narrow, store.
+template <class TIn, class TOut>
+__device__ __forceinline__ void store_row(uint64_t vL, uint64_t vR, uint64_t os2, bool scaled, TOut *dst,
+                                          int cols_valid, bool vec)
+{
+    if (scaled) {
+        vL = mul2(vL, os2);
+        vR = mul2(vR, os2);
+    }
+    float v[kColsPerThread];
+    if constexpr (Fmt<TIn>::kStride2) {
+        unpack2(vL, v[0], v[2]);
+        unpack2(vR, v[1], v[3]);
+    } else {
+        unpack2(vL, v[0], v[1]);
+        unpack2(vR, v[2], v[3]);
+    }
+    if (vec && cols_valid == kColsPerThread) {
+        Fmt<TOut>::store4(dst, v);
+    } else {
+#pragma unroll
+        for (int c = 0; c < kColsPerThread; ++c)
+            if (c < cols_valid) Fmt<TOut>::store1(dst + c, v[c]);
+    }
+}
+
+// One lane's strip, separable form: R output rows x 4 output columns.
 //   s:   shared memory at (first input row of the strip, first input column)
 //   out: global memory at (first output row, first output column)
 //   kk:  the taps as pairs (k[t], k[t]); os2 = (oscale, oscale)
-// Columns are processed as two pairs with packed FP32 arithmetic.  FP32 data
-// use column pairs (0,1) and (2,3): tap t multiplies the input pair
-// (a[c+t], a[c+t+1]), even t the aligned pairs E, odd t the shifted pairs O.
-// Narrow formats use column pairs (0,2) and (1,3): tap t multiplies the
-// stride-2 pair (a[c+t], a[c+t+2]).  Per element this is exactly hdot's
-// sequence: k0*a0, then fused multiply-adds for t = 1..4.
+// Per element this is exactly hdot's sequence for the row pass (k0*a0, then
+// fused multiply-adds for t = 1..4), and the same sequence down the column.
 template <class TIn, class TOut, int R, int BW>
 __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps],
                                            uint64_t os2, bool scaled, TOut *__restrict__ out,
                                            int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
 {
-    // accumulator pairs: columns (0,1) and (2,3), or (0,2) and (1,3) for stride-2 pairing
     uint64_t accL[R], accR[R];
 #pragma unroll
     for (int r = 0; r < R + kHalo; ++r) {
-        float a[8];
-        Fmt<TIn>::load8(s + r * BW, a);
-        uint64_t hL, hR;
-        if constexpr (Fmt<TIn>::kStride2) {
-            uint64_t S[6];
+        uint64_t PL[kTaps], PR[kTaps];
+        row_pairs<TIn>(s + r * BW, PL, PR);
+        uint64_t hL = mul2(kk[0], PL[0]);
+        uint64_t hR = mul2(kk[0], PR[0]);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) S[j] = pack2(a[j], a[j + 2]);
-            // (h0, h2) = sum_t k[t] (a[t], a[t+2]);  (h1, h3) = sum_t k[t] (a[t+1], a[t+3])
-            hL = mul2(kk[0], S[0]);
-            hR = mul2(kk[0], S[1]);
-#pragma unroll
-            for (int t = 1; t < kTaps; ++t) {
-                hL = fma2(kk[t], S[t], hL);
-                hR = fma2(kk[t], S[t + 1], hR);
-            }
-        } else {
-            const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
-            const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
-            const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
-            hL = mul2(kk[0], E0);
-            hL = fma2(kk[1], O0, hL);
-            hL = fma2(kk[2], E1, hL);
-            hL = fma2(kk[3], O1, hL);
-            hL = fma2(kk[4], E2, hL);
-            hR = mul2(kk[0], E1);
-            hR = fma2(kk[1], O1, hR);
-            hR = fma2(kk[2], E2, hR);
-            hR = fma2(kk[3], O2, hR);
-            hR = fma2(kk[4], E3, hR);
+        for (int t = 1; t < kTaps; ++t) {
+            hL = fma2(kk[t], PL[t], hL);
+            hR = fma2(kk[t], PR[t], hR);
         }
         // input row r carries tap t = r - o of output row o
 #pragma unroll
@@ -102,29 +132,48 @@ __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint
             }
         }
         const int o = r - kHalo;  // output row o has all five taps now
-        if (o >= 0 && o < rows_valid) {
-            uint64_t vL = accL[o], vR = accR[o];
-            if (scaled) {
-                vL = mul2(vL, os2);
-                vR = mul2(vR, os2);
-            }
-            float v[kColsPerThread];
-            if constexpr (Fmt<TIn>::kStride2) {
-                unpack2(vL, v[0], v[2]);
-                unpack2(vR, v[1], v[3]);
-            } else {
-                unpack2(vL, v[0], v[1]);
-                unpack2(vR, v[2], v[3]);
-            }
-            TOut *dst = out + static_cast<int64_t>(o) * out_pitch;
-            if (vec && cols_valid == kColsPerThread) {
-                Fmt<TOut>::store4(dst, v);
-            } else {
+        if (o >= 0 && o < rows_valid)
+            store_row<TIn, TOut>(accL[o], accR[o], os2, scaled, out + static_cast<int64_t>(o) * out_pitch,
+                                 cols_valid, vec);
+    }
+}
+
+// One lane's strip, direct form (the single-pass algorithm of Sec. 5.1 with
+// a general 5x5 matrix): every output is one FP32 chain of 25 products in the
+// row-major order of Eq. 3, K[0][0]*A[y][x] first, then fused multiply-adds
+// through K[4][4]*A[y+4][x+4].  KK holds the 25 entries as pairs (K, K).
+template <class TIn, class TOut, int R, int BW>
+__device__ __forceinline__ void conv_strip_direct(const TIn *__restrict__ s, const uint64_t (&KK)[kTaps * kTaps],
+                                                  uint64_t os2, bool scaled, TOut *__restrict__ out,
+                                                  int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
+{
+    uint64_t accL[R], accR[R];
 #pragma unroll
-                for (int c = 0; c < kColsPerThread; ++c)
-                    if (c < cols_valid) Fmt<TOut>::store1(dst + c, v[c]);
+    for (int r = 0; r < R + kHalo; ++r) {
+        uint64_t PL[kTaps], PR[kTaps];
+        row_pairs<TIn>(s + r * BW, PL, PR);
+        // input row r is kernel row i = r - o of output row o
+#pragma unroll
+        for (int i = 0; i < kTaps; ++i) {
+            const int o = r - i;
+            if (o >= 0 && o < R) {
+#pragma unroll
+                for (int j = 0; j < kTaps; ++j) {
+                    const uint64_t Kij = KK[i * kTaps + j];
+                    if (i == 0 && j == 0) {
+                        accL[o] = mul2(Kij, PL[0]);
+                        accR[o] = mul2(Kij, PR[0]);
+                    } else {
+                        accL[o] = fma2(Kij, PL[j], accL[o]);
+                        accR[o] = fma2(Kij, PR[j], accR[o]);
+                    }
+                }
             }
         }
+        const int o = r - kHalo;
+        if (o >= 0 && o < rows_valid)
+            store_row<TIn, TOut>(accL[o], accR[o], os2, scaled, out + static_cast<int64_t>(o) * out_pitch,
+                                 cols_valid, vec);
     }
 }
 
@@ -133,7 +182,7 @@ __device__ __forceinline__ void record_error(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
-template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH>
+template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH, bool DIRECT = false>
 __global__ void __launch_bounds__(32 * (TH / R + 1), 1)
 fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__ descs,
              const TileRec *__restrict__ tiles, int64_t ntiles, int *status)
@@ -204,6 +253,7 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
     // ---------------------------------------------------------------- consumers
     // Per-image fields in registers: once for a single image, per tile in a batch.
     uint64_t kk[kTaps];
+    uint64_t KK[DIRECT ? kTaps * kTaps : 1];
     uint64_t os2 = 0;
     bool scaled = false;
     unsigned char *out_base = nullptr;
@@ -211,8 +261,13 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
     int Hv = 0, Wv = 0;
     bool vec = false;
     auto load_desc = [&](const ImgDesc &d) {
+        if constexpr (DIRECT) {
 #pragma unroll
-        for (int q = 0; q < kTaps; ++q) kk[q] = pack2(d.k[q], d.k[q]);
+            for (int q = 0; q < kTaps * kTaps; ++q) KK[q] = pack2(d.K[q], d.K[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < kTaps; ++q) kk[q] = pack2(d.k[q], d.k[q]);
+        }
         os2 = pack2(d.oscale, d.oscale);
         scaled = d.oscale != 1.f;  // multiplying by exactly 1 would change nothing
         out_base = static_cast<unsigned char *>(d.out);
@@ -244,7 +299,10 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
                              (warp * R) * BW + lane * kColsPerThread;
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
-            conv_strip<TIn, TOut, R, BW>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
+            if constexpr (DIRECT)
+                conv_strip_direct<TIn, TOut, R, BW>(src, KK, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
+            else
+                conv_strip<TIn, TOut, R, BW>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -261,13 +319,13 @@ struct FusedEntry {
     int threads;
 };
 
-template <class TIn, class TOut, int TH, int TW, int R, int S>
+template <class TIn, class TOut, int TH, int TW, int R, int S, bool DIRECT = false>
 FusedEntry make_entry()
 {
     FusedEntry e;
     e.shape = FusedShape{TH, TW, R, S};
-    e.single_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, false>);
-    e.batch_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, true>);
+    e.single_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, false, DIRECT>);
+    e.batch_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, true, DIRECT>);
     e.smem = S * fused_stage_bytes<TIn, TH, TW>();
     e.threads = 32 * (TH / R + 1);
     return e;

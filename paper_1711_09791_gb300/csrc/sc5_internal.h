@@ -31,7 +31,8 @@ struct alignas(64) ImgDesc {
     float k[kTaps];
     float oscale;          // out_scale / in_scale
     int32_t vec;           // 1: 4-wide vector stores are aligned
-    int32_t pad_[5];
+    float K[kTaps * kTaps];  // direct form: the 5x5 matrix, row-major, K[i][j] at offset (i-2, j-2)
+    int32_t pad_[12];
 };
 static_assert(sizeof(ImgDesc) % 64 == 0, "ImgDesc must keep the tensor map 64-byte aligned");
 
@@ -45,20 +46,22 @@ struct FusedShape {
     int tile_h, tile_w, rows_per_thread, stages;
 };
 
-// Fused kernel launchers (sc5_fused.cu).  Return a cudaError_t.
-int fused_num_shapes(int in_dtype, int out_dtype);
-bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s);
-int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages);
+// Fused kernel launchers (sc5_fused.cu).  Return a cudaError_t.  `direct`
+// selects the direct single-pass kernels (25 products per output, K from the
+// descriptor); they have their own shape list.
+int fused_num_shapes(int in_dtype, int out_dtype, bool direct = false);
+bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct = false);
+int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct = false);
 // Bytes of dynamic shared memory and threads per CTA of a shape.
 int fused_smem_bytes(int in_dtype, const FusedShape &s);
 int fused_threads(const FusedShape &s);
 // Max resident CTAs per SM for a shape (occupancy query), or <= 0 on error.
-int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx);
+int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct = false);
 // Set the kernel attributes of a shape on the current device (call before
 // capturing a launch into a graph).
-cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx);
+cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct = false);
 cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgDesc &d,
-                                int64_t ntiles, int grid, cudaStream_t st);
+                                int64_t ntiles, int grid, cudaStream_t st, bool direct = false);
 cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDesc *descs,
                                const TileRec *tiles, int64_t ntiles, int grid, cudaStream_t st);
 cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code);
@@ -83,7 +86,8 @@ sc5_status fail(sc5_status st, const char *fmt, ...);
 sc5_status fail_cuda(cudaError_t e, const char *what);
 void clear_error();
 // Fused shape and CTAs/SM for a plane size (override > tuned table > default).
-sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas);
+sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
+                        bool direct = false);
 // Shape for a set of images: tuned choice for the size class with most pixels.
 sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas);
 // Host image of a batch launch: ImgDesc[n] then (256-byte aligned) TileRec[tiles].

@@ -22,7 +22,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EAGAIN", "ETIMEDOUT", "ENOTF
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8e4m3": 3}
 DTYPE_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "fp8e4m3": 1}
 BORDERS = {"valid": 0, "keep": 1}
-ALGOS = {"fused": 0, "two_pass": 1}
+ALGOS = {"fused": 0, "two_pass": 1, "direct": 2}
 
 
 class Sepconv5Error(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "sepconv5_plan_destroy": [V],
         "sepconv5_run": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_run_host": [V, V, V, POINTER(c_float), c_float, c_float, V],
+        "sepconv5_run_K": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_hpass": [V, V, V, c_int64, POINTER(c_float), V],
         "sepconv5_vpass": [V, V, c_int64, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_device_status": [V, POINTER(c_int32)],
@@ -174,6 +175,14 @@ class Plan:
     def run(self, src, dst, k, in_scale=1.0, out_scale=1.0, stream=None):
         _check(load().sepconv5_run(self._h, _ptr(src), _ptr(dst), _taps(k), in_scale, out_scale,
                                    _stream(stream)), "sepconv5_run")
+
+    def run_K(self, src, dst, K, in_scale=1.0, out_scale=1.0, stream=None):
+        """Direct form with a general 5x5 matrix K (25 values, row-major)."""
+        vals = [float(v) for row in K for v in (row if hasattr(row, "__iter__") else [row])]
+        if len(vals) != 25:
+            raise ValueError("K needs 25 values")
+        _check(load().sepconv5_run_K(self._h, _ptr(src), _ptr(dst), (c_float * 25)(*vals), in_scale, out_scale,
+                                     _stream(stream)), "sepconv5_run_K")
 
     def run_host(self, host_src, host_dst, k, in_scale=1.0, out_scale=1.0, stream=None):
         """host_src / host_dst: host addresses (or objects with data_ptr(), e.g.

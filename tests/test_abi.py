@@ -30,7 +30,7 @@ def test_fused_configs_listed(sc5):
     for pair in [("f32", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
                  ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]:
         cfgs = sc5.fused_configs(*pair)
-        assert cfgs and all(tw == 128 and th % 32 == 0 and st >= 2 for th, tw, st in cfgs)
+        assert cfgs and all(tw == 128 and th % 8 == 0 and 32 <= th + 4 <= 256 and st >= 2 for th, tw, st in cfgs)
         # a plan selects a shape by (tile_h, tile_w, stages): every triple must be unique
         assert len(set(cfgs)) == len(cfgs)
     with pytest.raises(sc5.Sepconv5Error):
