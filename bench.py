@@ -527,6 +527,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                         "unit": "Mpix/s", "achieved_gbs": round(alg / (ms3 / 1e3) / 1e9, 1),
                                         "frac_of_measured_hbm": round(alg / (ms3 / 1e3) / 1e9 / peak, 4),
                                         "vs_fused": round(ms3 / ms, 3)}
+        # in place: Listing 1's two-pass structure vs the single pass with copy-back
+        A_ip = A_dev.clone()
+        ip = {}
+        for algo in ("two_pass", "fused"):
+            pl = sepconv5.Plan(P, H, W, W, W, border="keep", algo=algo)
+            msi, _ = timed(lambda: pl.run_inplace(A_ip, k, stream=stream), k2, 3)
+            pl.close()
+            ip[algo] = {"ms_per_step": round(msi, 5), "vs_out_of_place_fused": round(msi / ms, 3)}
+        del A_ip
+        extras["in_place"] = {"two_pass_listing1": ip["two_pass"], "single_pass_copy_back": ip["fused"]}
         extras["two_pass"] = {"ms_per_step": round(ms2, 5), "value": round(world * pixels / (ms2 / 1e3) / 1e6, 1),
                               "unit": "Mpix/s", "achieved_gbs": round(alg / (ms2 / 1e3) / 1e9, 1),
                               "frac_of_measured_hbm": round(alg / (ms2 / 1e3) / 1e9 / peak, 4),

@@ -153,6 +153,21 @@ SC5_API sc5_status sepconv5_run(sc5_plan plan, const void *in, void *out, const 
 SC5_API sc5_status sepconv5_run_K(sc5_plan plan, const void *in, void *out, const float K[25],
                                   float in_scale, float out_scale, void *stream);
 
+/* In-place form: `img` (dev, [planes][H][in_pitch], the plan's in_dtype) is
+ * replaced by its convolution -- the interior pixels (2 <= y < H-2,
+ * 2 <= x < W-2) get the result, the 2-pixel frame keeps its values -- which is
+ * the image Listing 1 leaves in A.  The plan must have in_dtype == out_dtype,
+ * border SC5_BORDER_KEEP and out_pitch == in_pitch.  A stored code means
+ * value(c)/scale before and after.  By algo:
+ *   SC5_ALGO_TWO_PASS  Listing 1's structure: horizontal pass img -> T (the
+ *                      plan's FP32 intermediate), vertical pass T -> img;
+ *   SC5_ALGO_FUSED / SC5_ALGO_DIRECT  the single pass "with copy-back" of
+ *                      Sec. 5.2: convolve into a scratch image owned by the
+ *                      plan (allocated on the first call), then copy it back.
+ * Both move every pixel through HBM twice (the "two assignment operations"
+ * of Sec. 7).  Asynchronous on `stream`. */
+SC5_API sc5_status sepconv5_run_inplace(sc5_plan plan, void *img, const float k[5], float scale, void *stream);
+
 /* Offload form (the co-processor model of Sec. 7: copy the image to the
  * device, convolve, copy the result back): host_in and host_out are HOST
  * pointers laid out as for sepconv5_run (pinned memory gives full copy

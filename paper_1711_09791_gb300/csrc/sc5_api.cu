@@ -208,6 +208,8 @@ struct sc5_plan_s {
     size_t ws_host_cap = 0;
     cudaEvent_t ws_done = nullptr;
     bool ws_pending = false;
+    // copy-back scratch (sepconv5_run_inplace with a single-pass algo)
+    void *scratch = nullptr;
     // offload staging (sepconv5_run_host)
     void *stage_in = nullptr;
     void *stage_out = nullptr;
@@ -302,6 +304,7 @@ extern "C" sc5_status sepconv5_plan_destroy(sc5_plan p)
     cudaEventDestroy(p->ws_done);
     cudaFree(p->stage_in);
     cudaFree(p->stage_out);
+    cudaFree(p->scratch);
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -394,6 +397,47 @@ extern "C" sc5_status sepconv5_run_K(sc5_plan p, const void *in, void *out, cons
     st = run_single_pass(p, in, out, zero_k, K, in_scale, out_scale, s);
     if (st != SC5_OK) return st;
     return run_frame(d, in, out, in_scale, out_scale, s);
+}
+
+extern "C" sc5_status sepconv5_run_inplace(sc5_plan p, void *img, const float k[5], float scale, void *stream)
+{
+    clear_error();
+    if (!p || !img || !k) return fail(SC5_EINVAL, "null argument");
+    const sc5_plan_desc &d = p->d;
+    if (d.in_dtype != d.out_dtype || d.border != SC5_BORDER_KEEP || d.out_pitch != d.in_pitch)
+        return fail(SC5_EINVAL, "in-place needs in_dtype == out_dtype, border KEEP and out_pitch == in_pitch");
+    if (reinterpret_cast<uintptr_t>(img) % 16) return fail(SC5_EINVAL, "image must be 16-byte aligned");
+    if (!(scale > 0.f) || !std::isfinite(scale)) return fail(SC5_EINVAL, "scale must be finite and > 0");
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int es = dtype_bytes(d.in_dtype);
+    const int Hv = d.H - kHalo, Wv = d.W - kHalo;
+    char *base = static_cast<char *>(img);
+    char *interior = base + (2 * d.in_pitch + 2) * es;
+    const int64_t plane = static_cast<int64_t>(d.H) * d.in_pitch;
+    if (d.algo == SC5_ALGO_TWO_PASS) {
+        cudaError_t e = launch_hpass(d.in_dtype, img, d.planes, d.H, d.W, d.in_pitch, p->T, p->t_pitch, k, s);
+        if (e != cudaSuccess) return fail_cuda(e, "hpass launch");
+        e = launch_vpass(d.out_dtype, p->T, d.planes, d.H, Wv, p->t_pitch, interior, d.in_pitch, plane, k, 1.f,
+                         false, s);
+        return e == cudaSuccess ? SC5_OK : fail_cuda(e, "vpass launch");
+    }
+    // single pass into the scratch (VALID layout, pitch rounded to 16 bytes), then copy back
+    const int64_t sp = (static_cast<int64_t>(Wv) * es + 15) / 16 * 16 / es;
+    if (!p->scratch) {
+        cudaError_t e = cudaMalloc(&p->scratch, static_cast<size_t>(d.planes) * Hv * sp * es);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc of the copy-back scratch");
+    }
+    sc5_plan_desc vd = d;
+    vd.border = SC5_BORDER_VALID;
+    vd.out_pitch = sp;
+    sc5_plan_s tmp = *p;
+    tmp.d = vd;
+    sc5_status st = run_single_pass(&tmp, img, p->scratch, k, nullptr, scale, scale, s);
+    if (st != SC5_OK) return st;
+    cudaError_t e = launch_copy_interior(d.in_dtype, p->scratch, sp, static_cast<int64_t>(Hv) * sp, interior,
+                                         d.in_pitch, plane, d.planes, Hv, Wv, s);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "copy-back");
 }
 
 extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *host_out, const float k[5],

@@ -77,6 +77,10 @@ cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P
                               int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
                               cudaStream_t st);
 cudaError_t launch_empty(int n, cudaStream_t st);
+// Copy a VALID image into an interior that starts 2 elements into its rows
+// (src rows 16-byte aligned, dst interior 2*element-size aligned).
+cudaError_t launch_copy_interior(int dtype, const void *src, int64_t src_pitch, int64_t src_plane, void *dst,
+                                 int64_t dst_pitch, int64_t dst_plane, int P, int rows, int cols, cudaStream_t st);
 
 // Library-wide helpers (sc5_api.cu).
 void note_launches(int64_t n);

@@ -132,6 +132,56 @@ __global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int6
     }
 }
 
+// Copy a VALID image (rows 16-byte aligned, 4-element groups) into the
+// interior of an image whose interior starts 2 elements into a row: each
+// thread moves 4 elements with one aligned load and two half-width stores
+// (2 elements = half a group keeps both halves aligned).
+template <class T, class Half, class Group>
+__global__ void copy_interior_kernel(const T *__restrict__ src, int64_t src_pitch, int64_t src_plane,
+                                     T *__restrict__ dst, int64_t dst_pitch, int64_t dst_plane, int cols)
+{
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (x >= cols) return;
+    const int y = blockIdx.y, p = blockIdx.z;
+    const T *s = src + p * src_plane + static_cast<int64_t>(y) * src_pitch + x;
+    T *d = dst + p * dst_plane + static_cast<int64_t>(y) * dst_pitch + x;
+    if (x + 4 <= cols) {
+        const Group g = *reinterpret_cast<const Group *>(s);
+        const Half *h = reinterpret_cast<const Half *>(&g);
+        reinterpret_cast<Half *>(d)[0] = h[0];
+        reinterpret_cast<Half *>(d)[1] = h[1];
+    } else {
+        for (int c = 0; x + c < cols; ++c) d[c] = s[c];
+    }
+}
+
+cudaError_t launch_copy_interior(int dtype, const void *src, int64_t src_pitch, int64_t src_plane, void *dst,
+                                 int64_t dst_pitch, int64_t dst_plane, int P, int rows, int cols, cudaStream_t st)
+{
+    const dim3 grid((cols / 4 + 1 + 127) / 128, rows, P);
+    switch (dtype) {
+    case SC5_F32:
+        copy_interior_kernel<float, float2, float4><<<grid, 128, 0, st>>>(
+            static_cast<const float *>(src), src_pitch, src_plane, static_cast<float *>(dst), dst_pitch, dst_plane, cols);
+        break;
+    case SC5_BF16:
+    case SC5_F16:
+        copy_interior_kernel<uint16_t, uint32_t, uint2><<<grid, 128, 0, st>>>(
+            static_cast<const uint16_t *>(src), src_pitch, src_plane, static_cast<uint16_t *>(dst), dst_pitch,
+            dst_plane, cols);
+        break;
+    case SC5_FP8E4M3:
+        copy_interior_kernel<uint8_t, uint16_t, uint32_t><<<grid, 128, 0, st>>>(
+            static_cast<const uint8_t *>(src), src_pitch, src_plane, static_cast<uint8_t *>(dst), dst_pitch,
+            dst_plane, cols);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) note_launches(1);
+    return err;
+}
+
 __global__ void empty_kernel() {}
 
 // ------------------------------------------------------------------ launchers

@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "sepconv5_run": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_run_host": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_run_K": [V, V, V, POINTER(c_float), c_float, c_float, V],
+        "sepconv5_run_inplace": [V, V, POINTER(c_float), c_float, V],
         "sepconv5_hpass": [V, V, V, c_int64, POINTER(c_float), V],
         "sepconv5_vpass": [V, V, c_int64, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_device_status": [V, POINTER(c_int32)],
@@ -183,6 +184,10 @@ class Plan:
             raise ValueError("K needs 25 values")
         _check(load().sepconv5_run_K(self._h, _ptr(src), _ptr(dst), (c_float * 25)(*vals), in_scale, out_scale,
                                      _stream(stream)), "sepconv5_run_K")
+
+    def run_inplace(self, img, k, scale=1.0, stream=None):
+        _check(load().sepconv5_run_inplace(self._h, _ptr(img), _taps(k), scale, _stream(stream)),
+               "sepconv5_run_inplace")
 
     def run_host(self, host_src, host_dst, k, in_scale=1.0, out_scale=1.0, stream=None):
         """host_src / host_dst: host addresses (or objects with data_ptr(), e.g.
