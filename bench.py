@@ -527,6 +527,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                         "unit": "Mpix/s", "achieved_gbs": round(alg / (ms3 / 1e3) / 1e9, 1),
                                         "frac_of_measured_hbm": round(alg / (ms3 / 1e3) / 1e9 / peak, 4),
                                         "vs_fused": round(ms3 / ms, 3)}
+        # the 3R x C agglomerated layout of Sec. 6 (rows of the 3 planes side by side)
+        X = A_dev.permute(1, 0, 2).contiguous()
+        Y = torch.empty((H - 4, P, W - 4), dtype=torch.float32, device=dev)
+        pl = sepconv5.Plan(P, H, W, P * W, P * (W - 4), in_plane_stride=W, out_plane_stride=W - 4)
+        msl, _ = timed(lambda: pl.run(X, Y, k, stream=stream), k2, 3)
+        pl.close()
+        del X, Y
+        extras["layout_3RxC"] = {"ms_per_step": round(msl, 5), "frac_of_measured_hbm": round(alg / (msl / 1e3) / 1e9 / peak, 4),
+                                 "vs_stacked": round(msl / ms, 3)}
         # in place: Listing 1's two-pass structure vs the single pass with copy-back
         A_ip = A_dev.clone()
         ip = {}

@@ -97,9 +97,20 @@ typedef enum {
                                FP32, sepconv5_run_K takes any K */
 } sc5_algo;
 
-/* Plan descriptor.  Pitches are in elements of the respective dtype.
- * tile_h/tile_w/stages: 0 = take the autotuned (or built-in default) choice;
- * otherwise one of the compiled fused-kernel shapes (sepconv5_fused_configs). */
+/* Plan descriptor.  Pitches and plane strides are in elements of the
+ * respective dtype.  tile_h/tile_w/stages: 0 = take the autotuned (or
+ * built-in default) choice; otherwise one of the compiled fused-kernel shapes
+ * (sepconv5_fused_configs).
+ * Plane strides: 0 = planes stacked ([planes][H][pitch]: H*in_pitch for the
+ * input, Hout*out_pitch for the output).  Any other value places plane p at
+ * p*stride; the planes may then be stacked (stride >= H*pitch) or
+ * row-interleaved (stride >= W and pitch >= planes*stride), e.g. the 3R x C
+ * agglomeration of Sec. 6 where one row holds the rows of all 3 planes side
+ * by side: in_pitch = 3*W', in_plane_stride = W'.  The input plane stride
+ * times the element size must be a multiple of 16 bytes.  Non-default
+ * strides are supported by sepconv5_run, sepconv5_run_K and the two-pass
+ * entry points; batches, the offload call and the in-place call take
+ * stacked planes. */
 typedef struct {
     int32_t planes, H, W;
     int64_t in_pitch, out_pitch;
@@ -108,6 +119,7 @@ typedef struct {
     int32_t algo;                  /* sc5_algo */
     int32_t tile_h, tile_w, stages;
     int32_t ctas_per_sm;           /* 0 = as many as fit */
+    int64_t in_plane_stride, out_plane_stride;
 } sc5_plan_desc;
 
 typedef struct sc5_plan_s *sc5_plan;

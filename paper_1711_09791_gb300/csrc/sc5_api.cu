@@ -90,8 +90,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 // 3-D map of a planar image (x = column, y = row, z = plane), box of
 // box_w x box_h x 1 elements, zero fill outside the image.
 static sc5_status encode_image_map(CUtensorMap *m, int dtype, const void *base, int P, int H, int W,
-                                   int64_t pitch, int box_w, int box_h)
+                                   int64_t pitch, int box_w, int box_h, int64_t plane_stride = 0)
 {
+    if (plane_stride <= 0) plane_stride = pitch * H;
     auto fn = encode_fn();
     if (!fn) return fail(SC5_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const int es = dtype_bytes(dtype);
@@ -101,7 +102,7 @@ static sc5_status encode_image_map(CUtensorMap *m, int dtype, const void *base, 
     const cuuint64_t dims[3] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H),
                                 static_cast<cuuint64_t>(P)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(pitch) * es,
-                                   static_cast<cuuint64_t>(pitch) * es * static_cast<cuuint64_t>(H)};
+                                   static_cast<cuuint64_t>(plane_stride) * es};
     const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, t, 3, const_cast<void *>(base), dims, strides, box, estr,
@@ -119,9 +120,16 @@ static int box_w_for(int dtype, int tile_w)
 
 // ------------------------------------------------------------------ validation
 
+// Planes of an image do not overlap: stacked (stride >= rows * pitch) or
+// row-interleaved (stride >= width and pitch >= planes * stride).
+static bool planes_disjoint(int P, int64_t rows, int64_t width, int64_t pitch, int64_t stride)
+{
+    return P == 1 || stride >= rows * pitch || (stride >= width && pitch >= P * stride);
+}
+
 static sc5_status check_image(int in_dtype, int out_dtype, int border, const void *in, const void *out,
                               int P, int H, int W, int64_t in_pitch, int64_t out_pitch, float in_scale,
-                              float out_scale, bool need_ptrs)
+                              float out_scale, bool need_ptrs, int64_t in_ps = 0, int64_t out_ps = 0)
 {
     if (P < 1 || H < 5 || W < 5) return fail(SC5_EINVAL, "need planes >= 1, H >= 5, W >= 5 (got %d, %d, %d)", P, H, W);
     if (H > 65535 * 8 || W > (1 << 30)) return fail(SC5_EINVAL, "image too large (H <= 524280, W < 2^30)");
@@ -132,6 +140,13 @@ static sc5_status check_image(int in_dtype, int out_dtype, int border, const voi
     if (in_pitch < W) return fail(SC5_EINVAL, "in_pitch %lld < W %d", (long long)in_pitch, W);
     if (out_pitch < wout) return fail(SC5_EINVAL, "out_pitch %lld < output width %lld", (long long)out_pitch, (long long)wout);
     if ((in_pitch * ei) % 16) return fail(SC5_EINVAL, "in_pitch * element size must be a multiple of 16 bytes");
+    const int64_t hout = border == SC5_BORDER_KEEP ? H : H - kHalo;
+    if (in_ps < 0 || out_ps < 0) return fail(SC5_EINVAL, "negative plane stride");
+    if (in_ps == 0) in_ps = static_cast<int64_t>(H) * in_pitch;
+    if (out_ps == 0) out_ps = hout * out_pitch;
+    if ((in_ps * ei) % 16) return fail(SC5_EINVAL, "in_plane_stride * element size must be a multiple of 16 bytes");
+    if (!planes_disjoint(P, H, W, in_pitch, in_ps) || !planes_disjoint(P, hout, wout, out_pitch, out_ps))
+        return fail(SC5_EINVAL, "plane stride makes planes overlap (need stacked or row-interleaved planes)");
     if ((static_cast<double>(in_pitch) * ei * H * P) >= 1099511627776.0) return fail(SC5_EINVAL, "image larger than 2^40 bytes");
     if (!(in_scale > 0.f) || !std::isfinite(in_scale) || !(out_scale > 0.f) || !std::isfinite(out_scale))
         return fail(SC5_EINVAL, "scales must be finite and > 0");
@@ -140,9 +155,9 @@ static sc5_status check_image(int in_dtype, int out_dtype, int border, const voi
         if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
         if (reinterpret_cast<uintptr_t>(out) % eo) return fail(SC5_EINVAL, "output not aligned to its element size");
         const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
-        const char *a_end = a + static_cast<size_t>(P) * H * in_pitch * ei;
-        const int64_t hout = border == SC5_BORDER_KEEP ? H : H - kHalo;
-        const char *b_end = b + static_cast<size_t>(P) * hout * out_pitch * eo;
+        // one past the last element of the last row of the last plane
+        const char *a_end = a + (static_cast<size_t>(P - 1) * in_ps + static_cast<size_t>(H - 1) * in_pitch + W) * ei;
+        const char *b_end = b + (static_cast<size_t>(P - 1) * out_ps + static_cast<size_t>(hout - 1) * out_pitch + wout) * eo;
         if (a < b_end && b < a_end) return fail(SC5_EINVAL, "input and output overlap");
     }
     return SC5_OK;
@@ -155,15 +170,32 @@ static bool taps_finite(const float *k)
     return true;
 }
 
+// Effective plane strides of a plan (elements).
+static int64_t in_plane_of(const sc5_plan_desc &d)
+{
+    return d.in_plane_stride > 0 ? d.in_plane_stride : static_cast<int64_t>(d.H) * d.in_pitch;
+}
+
+static int64_t out_plane_of(const sc5_plan_desc &d)
+{
+    const int64_t hout = d.border == SC5_BORDER_KEEP ? d.H : d.H - kHalo;
+    return d.out_plane_stride > 0 ? d.out_plane_stride : hout * d.out_pitch;
+}
+
+static bool default_strides(const sc5_plan_desc &d)
+{
+    return d.in_plane_stride == 0 && d.out_plane_stride == 0;
+}
+
 // Fill an ImgDesc for one image (tensor map included).
 static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border, const FusedShape &sh,
                             const void *in, void *out, int P, int H, int W, int64_t in_pitch,
                             int64_t out_pitch, const float *k, float in_scale, float out_scale,
-                            const float *K = nullptr)
+                            const float *K = nullptr, int64_t in_ps = 0, int64_t out_ps = 0)
 {
     std::memset(d, 0, sizeof *d);
     sc5_status st = encode_image_map(&d->tmap, in_dtype, in, P, H, W, in_pitch,
-                                     box_w_for(in_dtype, sh.tile_w), sh.tile_h + kHalo);
+                                     box_w_for(in_dtype, sh.tile_w), sh.tile_h + kHalo, in_ps);
     if (st != SC5_OK) return st;
     const int eo = dtype_bytes(out_dtype);
     char *ob = static_cast<char *>(out);
@@ -174,7 +206,7 @@ static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border,
     }
     d->out = ob;
     d->out_pitch = out_pitch;
-    d->out_plane = plane_rows * out_pitch;
+    d->out_plane = out_ps > 0 ? out_ps : plane_rows * out_pitch;
     d->Hv = H - kHalo;
     d->Wv = W - kHalo;
     d->tiles_x = (d->Wv + sh.tile_w - 1) / sh.tile_w;
@@ -256,7 +288,7 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS && d.algo != SC5_ALGO_DIRECT)
         return fail(SC5_EINVAL, "unknown algo %d", d.algo);
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
-                                d.in_pitch, d.out_pitch, 1.f, 1.f, false);
+                                d.in_pitch, d.out_pitch, 1.f, 1.f, false, d.in_plane_stride, d.out_plane_stride);
     if (st != SC5_OK) return st;
     if (!pair_supported(d.in_dtype, d.out_dtype))
         return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built: the output must be the input format or FP32",
@@ -316,19 +348,17 @@ static sc5_status run_two_pass(sc5_plan p, const void *in, void *out, const floa
                                float out_scale, cudaStream_t st)
 {
     const sc5_plan_desc &d = p->d;
-    cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, p->T, p->t_pitch, k, st);
+    cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, p->T, p->t_pitch, k, st,
+                                 in_plane_of(d));
     if (e != cudaSuccess) return fail_cuda(e, "hpass launch");
     const int eo = dtype_bytes(d.out_dtype);
     char *ob = static_cast<char *>(out);
-    int64_t plane_rows = d.H - kHalo;
-    if (d.border == SC5_BORDER_KEEP) {
-        ob += (2 * d.out_pitch + 2) * eo;
-        plane_rows = d.H;
-    }
-    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0;
+    if (d.border == SC5_BORDER_KEEP) ob += (2 * d.out_pitch + 2) * eo;
+    const int64_t op = out_plane_of(d);
+    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0 && op % 4 == 0;
     const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
-    e = launch_vpass(d.out_dtype, p->T, d.planes, d.H, d.W - kHalo, p->t_pitch, ob, d.out_pitch,
-                     plane_rows * d.out_pitch, k, oscale, vec, st);
+    e = launch_vpass(d.out_dtype, p->T, d.planes, d.H, d.W - kHalo, p->t_pitch, ob, d.out_pitch, op, k, oscale,
+                     vec, st);
     if (e != cudaSuccess) return fail_cuda(e, "vpass launch");
     return SC5_OK;
 }
@@ -339,7 +369,7 @@ static sc5_status run_frame(const sc5_plan_desc &d, const void *in, void *out, f
     if (d.border != SC5_BORDER_KEEP) return SC5_OK;
     const float ratio = static_cast<float>(static_cast<double>(out_scale) / in_scale);
     cudaError_t e = launch_keep_frame(d.in_dtype, d.out_dtype, in, d.planes, d.H, d.W, d.in_pitch, out,
-                                      d.out_pitch, ratio, st);
+                                      d.out_pitch, ratio, st, in_plane_of(d), out_plane_of(d));
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "frame launch");
 }
 
@@ -350,7 +380,9 @@ static sc5_status run_single_pass(sc5_plan p, const void *in, void *out, const f
     const sc5_plan_desc &d = p->d;
     ImgDesc desc;
     sc5_status st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, in, out, d.planes, d.H, d.W,
-                              d.in_pitch, d.out_pitch, k, in_scale, out_scale, K);
+                              d.in_pitch, d.out_pitch, k, in_scale, out_scale, K, d.in_plane_stride,
+                              d.out_plane_stride);
+    if (desc.out_plane % 4) desc.vec = 0;
     if (st != SC5_OK) return st;
     const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
     const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
@@ -367,7 +399,7 @@ extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const 
     if (!p || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
-                                d.out_pitch, in_scale, out_scale, true);
+                                d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride);
     if (st != SC5_OK) return st;
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -388,7 +420,7 @@ extern "C" sc5_status sepconv5_run_K(sc5_plan p, const void *in, void *out, cons
     const sc5_plan_desc &d = p->d;
     if (d.algo != SC5_ALGO_DIRECT) return fail(SC5_EINVAL, "sepconv5_run_K needs a plan with algo SC5_ALGO_DIRECT");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
-                                d.out_pitch, in_scale, out_scale, true);
+                                d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride);
     if (st != SC5_OK) return st;
     for (int i = 0; i < kTaps * kTaps; ++i)
         if (!std::isfinite(K[i])) return fail(SC5_EINVAL, "K must be finite");
@@ -406,6 +438,7 @@ extern "C" sc5_status sepconv5_run_inplace(sc5_plan p, void *img, const float k[
     const sc5_plan_desc &d = p->d;
     if (d.in_dtype != d.out_dtype || d.border != SC5_BORDER_KEEP || d.out_pitch != d.in_pitch)
         return fail(SC5_EINVAL, "in-place needs in_dtype == out_dtype, border KEEP and out_pitch == in_pitch");
+    if (!default_strides(d)) return fail(SC5_EINVAL, "in-place takes stacked planes (plane strides 0)");
     if (reinterpret_cast<uintptr_t>(img) % 16) return fail(SC5_EINVAL, "image must be 16-byte aligned");
     if (!(scale > 0.f) || !std::isfinite(scale)) return fail(SC5_EINVAL, "scale must be finite and > 0");
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
@@ -446,6 +479,7 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
     clear_error();
     if (!p || !host_in || !host_out || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (!default_strides(d)) return fail(SC5_EINVAL, "the offload call takes stacked planes (plane strides 0)");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, false);
     if (st != SC5_OK) return st;
@@ -543,7 +577,7 @@ extern "C" sc5_status sepconv5_hpass(sc5_plan p, const void *in, float *T, int64
     if (d.H > 65535) return fail(SC5_EINVAL, "two-pass form needs H <= 65535");
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
     cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, T, t_pitch, k,
-                                 static_cast<cudaStream_t>(stream));
+                                 static_cast<cudaStream_t>(stream), in_plane_of(d));
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "hpass launch");
 }
 
@@ -560,15 +594,12 @@ extern "C" sc5_status sepconv5_vpass(sc5_plan p, const float *T, int64_t t_pitch
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
     const int eo = dtype_bytes(d.out_dtype);
     char *ob = static_cast<char *>(out);
-    int64_t plane_rows = d.H - kHalo;
-    if (d.border == SC5_BORDER_KEEP) {
-        ob += (2 * d.out_pitch + 2) * eo;
-        plane_rows = d.H;
-    }
-    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0;
+    if (d.border == SC5_BORDER_KEEP) ob += (2 * d.out_pitch + 2) * eo;
+    const int64_t op = out_plane_of(d);
+    const bool vec = reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && d.out_pitch % 4 == 0 && op % 4 == 0;
     const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
-    cudaError_t e = launch_vpass(d.out_dtype, T, d.planes, d.H, d.W - kHalo, t_pitch, ob, d.out_pitch,
-                                 plane_rows * d.out_pitch, k, oscale, vec, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_vpass(d.out_dtype, T, d.planes, d.H, d.W - kHalo, t_pitch, ob, d.out_pitch, op, k,
+                                 oscale, vec, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "vpass launch");
 }
 

@@ -69,13 +69,13 @@ cudaError_t launch_wait_selftest(int limit_us, cudaStream_t st);
 
 // Two-pass kernels and helpers (sc5_twopass.cu).
 cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,
-                         float *T, int64_t t_pitch, const float *k, cudaStream_t st);
+                         float *T, int64_t t_pitch, const float *k, cudaStream_t st, int64_t in_plane = 0);
 cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, int64_t t_pitch,
                          void *out, int64_t out_pitch, int64_t out_plane, const float *k,
                          float oscale, bool vec, cudaStream_t st);
 cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
                               int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
-                              cudaStream_t st);
+                              cudaStream_t st, int64_t in_plane = 0, int64_t out_plane = 0);
 cudaError_t launch_empty(int n, cudaStream_t st);
 // Copy a VALID image into an interior that starts 2 elements into its rows
 // (src rows 16-byte aligned, dst interior 2*element-size aligned).

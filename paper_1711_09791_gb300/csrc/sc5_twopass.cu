@@ -24,14 +24,14 @@ constexpr int kVRows = 8;  // output rows per thread in the vertical pass
 
 template <class TIn>
 __global__ void __launch_bounds__(kPassThreads)
-hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, float *__restrict__ T,
-             int64_t t_pitch, Taps taps)
+hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t in_plane,
+             float *__restrict__ T, int64_t t_pitch, Taps taps)
 {
     const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
     const int Wv = W - kHalo;
     if (x >= Wv) return;
     const int y = blockIdx.y, p = blockIdx.z;
-    const TIn *row = in + (static_cast<int64_t>(p) * H + y) * in_pitch + x;
+    const TIn *row = in + p * in_plane + static_cast<int64_t>(y) * in_pitch + x;
     float k[kTaps];
 #pragma unroll
     for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
@@ -108,8 +108,8 @@ vpass_kernel(const float *__restrict__ T, int H, int Wv, int64_t t_pitch, TOut *
 // The 2-pixel frame of a KEEP-border output: out = value(in) * ratio, stored
 // in the output format (an exact copy when formats and scales agree).
 template <class TIn, class TOut>
-__global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch,
-                                  TOut *__restrict__ out, int64_t out_pitch, float ratio)
+__global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t in_plane,
+                                  TOut *__restrict__ out, int64_t out_pitch, int64_t out_plane, float ratio)
 {
     const int64_t n_rows = 4ll * W;                 // rows 0, 1, H-2, H-1
     const int64_t n = n_rows + 4ll * (H - kHalo);   // plus cols 0, 1, W-2, W-1 of rows 2..H-3
@@ -127,8 +127,8 @@ __global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int6
             const int c = static_cast<int>(j % 4);
             x = (c < 2) ? c : W - 4 + c;
         }
-        const float v = Fmt<TIn>::load1(in + (static_cast<int64_t>(p) * H + y) * in_pitch + x);
-        Fmt<TOut>::store1(out + (static_cast<int64_t>(p) * H + y) * out_pitch + x, __fmul_rn(v, ratio));
+        const float v = Fmt<TIn>::load1(in + p * in_plane + static_cast<int64_t>(y) * in_pitch + x);
+        Fmt<TOut>::store1(out + p * out_plane + static_cast<int64_t>(y) * out_pitch + x, __fmul_rn(v, ratio));
     }
 }
 
@@ -194,24 +194,25 @@ static Taps make_taps(const float *k)
 }
 
 cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,
-                         float *T, int64_t t_pitch, const float *k, cudaStream_t st)
+                         float *T, int64_t t_pitch, const float *k, cudaStream_t st, int64_t in_plane)
 {
+    if (in_plane <= 0) in_plane = static_cast<int64_t>(H) * in_pitch;
     const int Wv = W - kHalo;
     const int groups = (Wv + kColsPerThread - 1) / kColsPerThread;
     const dim3 grid((groups + kPassThreads - 1) / kPassThreads, H, P);
     const Taps taps = make_taps(k);
     switch (in_dtype) {
     case SC5_F32:
-        hpass_kernel<float><<<grid, kPassThreads, 0, st>>>(static_cast<const float *>(in), H, W, in_pitch, T, t_pitch, taps);
+        hpass_kernel<float><<<grid, kPassThreads, 0, st>>>(static_cast<const float *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_BF16:
-        hpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const bf16_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        hpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const bf16_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_F16:
-        hpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const f16_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        hpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const f16_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_FP8E4M3:
-        hpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(static_cast<const fp8e4m3_t *>(in), H, W, in_pitch, T, t_pitch, taps);
+        hpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(static_cast<const fp8e4m3_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -250,16 +251,16 @@ cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, in
 }
 
 template <class TIn>
-static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, int64_t in_pitch,
-                             void *out, int64_t out_pitch, float ratio, cudaStream_t st)
+static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, int64_t in_pitch, int64_t in_plane,
+                             void *out, int64_t out_pitch, int64_t out_plane, float ratio, cudaStream_t st)
 {
     const int64_t n = 4ll * W + 4ll * (H - kHalo);
     const dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), P);
     switch (out_dtype) {
-    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<float *>(out), out_pitch, ratio); break;
-    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<bf16_t *>(out), out_pitch, ratio); break;
-    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<f16_t *>(out), out_pitch, ratio); break;
-    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, static_cast<fp8e4m3_t *>(out), out_pitch, ratio); break;
+    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<float *>(out), out_pitch, out_plane, ratio); break;
+    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<bf16_t *>(out), out_pitch, out_plane, ratio); break;
+    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<f16_t *>(out), out_pitch, out_plane, ratio); break;
+    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, ratio); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -267,14 +268,16 @@ static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, 
 
 cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
                               int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
-                              cudaStream_t st)
+                              cudaStream_t st, int64_t in_plane, int64_t out_plane)
 {
+    if (in_plane <= 0) in_plane = static_cast<int64_t>(H) * in_pitch;
+    if (out_plane <= 0) out_plane = static_cast<int64_t>(H) * out_pitch;
     cudaError_t err;
     switch (in_dtype) {
-    case SC5_F32: err = frame_out(out_dtype, static_cast<const float *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
-    case SC5_BF16: err = frame_out(out_dtype, static_cast<const bf16_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
-    case SC5_F16: err = frame_out(out_dtype, static_cast<const f16_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
-    case SC5_FP8E4M3: err = frame_out(out_dtype, static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, out, out_pitch, ratio, st); break;
+    case SC5_F32: err = frame_out(out_dtype, static_cast<const float *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
+    case SC5_BF16: err = frame_out(out_dtype, static_cast<const bf16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
+    case SC5_F16: err = frame_out(out_dtype, static_cast<const f16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
+    case SC5_FP8E4M3: err = frame_out(out_dtype, static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
     default: return cudaErrorInvalidValue;
     }
     if (err == cudaSuccess) note_launches(1);

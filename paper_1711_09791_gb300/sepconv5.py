@@ -36,7 +36,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("planes", c_int32), ("H", c_int32), ("W", c_int32),
                 ("in_pitch", c_int64), ("out_pitch", c_int64),
                 ("in_dtype", c_int32), ("out_dtype", c_int32), ("border", c_int32), ("algo", c_int32),
-                ("tile_h", c_int32), ("tile_w", c_int32), ("stages", c_int32), ("ctas_per_sm", c_int32)]
+                ("tile_h", c_int32), ("tile_w", c_int32), ("stages", c_int32), ("ctas_per_sm", c_int32),
+                ("in_plane_stride", c_int64), ("out_plane_stride", c_int64)]
 
 
 class Image(ctypes.Structure):
@@ -153,7 +154,7 @@ class Plan:
 
     def __init__(self, planes: int, H: int, W: int, in_pitch: int | None = None, out_pitch: int | None = None,
                  in_dtype="f32", out_dtype=None, border="valid", algo="fused", tile_h=0, tile_w=0, stages=0,
-                 ctas_per_sm=0):
+                 ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0):
         out_dtype = in_dtype if out_dtype is None else out_dtype
         b = BORDERS[border] if isinstance(border, str) else int(border)
         d = PlanDesc()
@@ -164,6 +165,7 @@ class Plan:
         d.border = b
         d.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
         d.tile_h, d.tile_w, d.stages, d.ctas_per_sm = tile_h, tile_w, stages, ctas_per_sm
+        d.in_plane_stride, d.out_plane_stride = in_plane_stride, out_plane_stride
         self.desc = d
         h = c_void_p()
         _check(load().sepconv5_plan(byref(d), byref(h)), "sepconv5_plan")
