@@ -12,6 +12,8 @@ to it.  Each wrapper names the passage of the paper it follows:
 * :func:`direct`        -- Eq. 1 with K = k k^T (Sec. 1), single-pass form
 * :func:`direct_K`      -- Eq. 1 with a general 5x5 K (Sec. 5.1, the
                            "general algorithm" with four nested loops)
+* :func:`direct_Kn`     -- Eq. 1 with a general n x n K, any odd width n
+* :func:`direct_n`      -- Eq. 1 with K = k k^T for a width-n vector k
 * :func:`hpass`         -- the horizontal 1D pass (Sec. 5.1, Listing 1)
 * :func:`vpass`         -- the vertical 1D pass (Sec. 5.1, Listing 1)
 * :func:`points_f32`    -- Eq. 1 at chosen output pixels of an FP32 image
@@ -68,6 +70,8 @@ def _bind(path: str):
     lib.sc5o_points_f32.argtypes = [P, I, I, I, I, P, P, I, P]
     lib.sc5o_decode.argtypes = [ctypes.c_int, P, I, ctypes.c_double, P]
     lib.sc5o_outer.argtypes = [P, P]
+    lib.sc5o_direct_Kn.argtypes = [P, I, I, I, I, P, P]
+    lib.sc5o_direct_Kn.restype = ctypes.c_int
     for f in ("sc5o_direct_K", "sc5o_direct", "sc5o_hpass", "sc5o_vpass",
               "sc5o_points_f32", "sc5o_decode"):
         getattr(lib, f).restype = ctypes.c_int
@@ -130,6 +134,28 @@ def direct(A, k) -> np.ndarray:
     if _load().sc5o_direct(_ptr(A), P, H, W, _ptr(k), _ptr(B)) != 0:
         raise ValueError("direct: image smaller than 5x5")
     return B
+
+
+def direct_Kn(A, K) -> np.ndarray:
+    """Eq. 1 with a general n x n K (n odd); VALID output [P][H-n+1][W-n+1]."""
+    A = _as3(A)
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    n = K.shape[0]
+    if K.shape != (n, n) or n % 2 == 0:
+        raise ValueError("K must be square with odd width")
+    P, H, W = A.shape
+    if H < n or W < n:
+        raise ValueError("direct_Kn: image smaller than the kernel")
+    B = np.empty((P, H - n + 1, W - n + 1), np.float64)
+    if _load().sc5o_direct_Kn(_ptr(A), P, H, W, n, _ptr(K), _ptr(B)) != 0:
+        raise ValueError("direct_Kn: bad sizes")
+    return B
+
+
+def direct_n(A, k) -> np.ndarray:
+    """Eq. 1 with K[i][j] = k[i] k[j] for a vector k of odd length n."""
+    k = np.ascontiguousarray(k, dtype=np.float64).reshape(-1)
+    return direct_Kn(A, np.outer(k, k))
 
 
 def hpass(A, k) -> np.ndarray:

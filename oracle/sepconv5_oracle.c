@@ -153,6 +153,33 @@ int sc5o_points_f32(const float *A, int64_t P, int64_t H, int64_t W, int64_t pit
     return 0;
 }
 
+/*
+ * Eq. 1 for a kernel of any odd width n (the width-5 routines above are the
+ * n = 5 case): B[p][y][x] = sum_{i<n} sum_{j<n} A[p][y+i][x+j] * K[i*n+j] on
+ * the VALID region, plane p of B being (H-n+1) x (W-n+1); output (y, x) is
+ * centred on input (y+r, x+r) with r = (n-1)/2, so K[i][j] sits at offset
+ * (i-r, j-r).  A separable kernel passes K[i][j] = k[i] * k[j].
+ */
+int sc5o_direct_Kn(const double *A, int64_t P, int64_t H, int64_t W, int64_t n,
+                   const double *K, double *B)
+{
+    if (n < 1 || n % 2 == 0 || P < 1 || H < n || W < n) return -1;
+    const int64_t Hv = H - n + 1, Wv = W - n + 1;
+    for (int64_t p = 0; p < P; ++p) {
+        const double *Ap = A + p * H * W;
+        double *Bp = B + p * Hv * Wv;
+        for (int64_t y = 0; y < Hv; ++y)
+            for (int64_t x = 0; x < Wv; ++x) {
+                double s = 0.0;
+                for (int64_t i = 0; i < n; ++i)
+                    for (int64_t j = 0; j < n; ++j)
+                        s += Ap[(y + i) * W + (x + j)] * K[i * n + j];
+                Bp[y * Wv + x] = s;
+            }
+    }
+    return 0;
+}
+
 /* ---- storage-format decoders (exact, from the published bit layouts) ---- */
 
 /* bfloat16: the upper 16 bits of an IEEE binary32 (1 sign, 8 exponent, 7 fraction). */

@@ -262,6 +262,60 @@ def pin_keep_frame():
     assert np.array_equal(F[:, 2:-2, 2:-2], B)
 
 
+WIDTHS = [1, 3, 7, 9]
+
+
+def pin_width_n_scipy_correlate2d():
+    from scipy.signal import correlate2d
+    g = synth.rng(91)
+    for n in WIDTHS:
+        for (H, W) in [(n, n), (n + 3, n + 8), (20, 31)]:
+            A = _rand_image(H * 13 + W + n, H, W, P=2)
+            K = g.uniform(-1, 1, size=(n, n))
+            B = oracle.direct_Kn(A, K)
+            for p in range(2):
+                ref = correlate2d(A[p], K, mode="valid")
+                assert B[p].shape == ref.shape
+                assert np.max(np.abs(B[p] - ref)) <= 1e-12 * 255 * n * n
+
+
+def pin_width_n_deltas_and_impulse():
+    for n in WIDTHS:
+        r = (n - 1) // 2
+        A = _rand_image(n, n + 6, n + 9)
+        for (i, j) in [(0, 0), (0, n - 1), (r, r), (n - 1, 0)]:
+            D = np.zeros((n, n))
+            D[i, j] = 1.0
+            assert np.array_equal(oracle.direct_Kn(A, D), A[:, i:i + 7, j:j + 10])
+        K = np.arange(n * n, dtype=np.float64).reshape(n, n) + 1.0
+        imp = np.zeros((1, 2 * n - 1, 2 * n - 1))
+        imp[0, n - 1, n - 1] = 1.0
+        assert np.array_equal(oracle.direct_Kn(imp, K)[0], K[::-1, ::-1])
+
+
+def pin_width_n_constant_and_integers():
+    for n in WIDTHS:
+        k = synth.rng(n).uniform(0, 1, n)
+        k /= k.sum()
+        c = 97.25
+        B = oracle.direct_n(np.full((1, n + 4, n + 5), c), k)
+        assert np.max(np.abs(B - c * k.sum() ** 2)) <= 16 * np.finfo(float).eps * c
+        A = synth.integer_image(n * 5, n + 3, n + 4, planes=1)
+        kint = list(range(1, n + 1))
+        B = oracle.direct_n(A.astype(np.float64), kint)
+        Ai = A.astype(np.int64).tolist()
+        for y in range(4):
+            for x in range(5):
+                s = sum(Ai[0][y + i][x + j] * kint[i] * kint[j] for i in range(n) for j in range(n))
+                assert B[0, y, x] == float(s)
+
+
+def pin_width_5_agrees_with_direct():
+    A = _rand_image(55, 12, 17)
+    k = _nonsym_k(55)
+    assert np.max(np.abs(oracle.direct_n(A, k) - oracle.direct(A, k))) <= 1e-12 * 255
+
+
 PINS = [v for n, v in sorted(globals().items()) if n.startswith("pin_")]
 
 
@@ -283,17 +337,27 @@ def test_bad_sizes_rejected():
 MUTANTS = {
     "dropped kernel column": ("for (int j = 0; j < SC5O_TAPS; ++j)\n                        s +=",
                               "for (int j = 0; j < SC5O_TAPS - 1; ++j)\n                        s +="),
-    "transposed image operand": ("Ap[(y + i) * W + (x + j)]", "Ap[(y + j) * W + (x + i)]"),
+    "transposed image operand": ("Ap[(y + i) * W + (x + j)] * K[i * SC5O_TAPS + j]",
+                                 "Ap[(y + j) * W + (x + i)] * K[i * SC5O_TAPS + j]"),
+    "width-n transposed image operand": ("Ap[(y + i) * W + (x + j)] * K[i * n + j]",
+                                         "Ap[(y + j) * W + (x + i)] * K[i * n + j]"),
     "transposed K": ("* K[i * SC5O_TAPS + j];\n                Bp", "* K[j * SC5O_TAPS + i];\n                Bp"),
     "flipped horizontal taps": ("W + x + t] * k[t]", "W + x + t] * k[4 - t]"),
     "flipped vertical taps": ("T[(p * H + y + t) * Wt + x] * k[t]", "T[(p * H + y + 4 - t) * Wt + x] * k[t]"),
     "outer product index": ("K[i * SC5O_TAPS + j] = k[i] * k[j]", "K[i * SC5O_TAPS + j] = k[i] * k[4 - j]"),
-    "sign error": ("s += Ap[", "s -= Ap["),
+    "sign error": ("s += Ap[(y + i) * W + (x + j)] * K[i * SC5O_TAPS + j]",
+                   "s -= Ap[(y + i) * W + (x + j)] * K[i * SC5O_TAPS + j]"),
+    "width-n sign error": ("s += Ap[(y + i) * W + (x + j)] * K[i * n + j]",
+                           "s -= Ap[(y + i) * W + (x + j)] * K[i * n + j]"),
     "points row offset": ("(p * H + y + i) * pitch + x + j]", "(p * H + y + i) * pitch + x + i]"),
     "e4m3 bias": ("ldexp(1.0 + (double)m / 8.0, e - 7)", "ldexp(1.0 + (double)m / 8.0, e - 8)"),
     "e4m3 subnormal": ("ldexp((double)m, -9)", "ldexp((double)m, -10)"),
     "f16 bias": ("ldexp(1.0 + (double)m / 1024.0, e - 15)", "ldexp(1.0 + (double)m / 1024.0, e - 14)"),
     "scale multiplies": ("out[i] = v / scale;", "out[i] = v * scale;"),
+    "width-n transposed K": ("* K[i * n + j];", "* K[j * n + i];"),
+    "width-n dropped row": ("for (int64_t i = 0; i < n; ++i)\n                    for (int64_t j = 0; j < n; ++j)",
+                            "for (int64_t i = 1; i < n; ++i)\n                    for (int64_t j = 0; j < n; ++j)"),
+    "width-n VALID size": ("const int64_t Hv = H - n + 1, Wv = W - n + 1;", "const int64_t Hv = H - n + 1, Wv = W - n;"),
 }
 
 
