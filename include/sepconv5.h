@@ -98,7 +98,13 @@ typedef enum {
 } sc5_algo;
 
 /* Plan descriptor.  Pitches and plane strides are in elements of the
- * respective dtype.  tile_h/tile_w/stages: 0 = take the autotuned (or
+ * respective dtype.
+ * taps: the kernel width n.  The paper uses 5 (Sec. 4); 3, 7 and 9 are built
+ * for SC5_ALGO_FUSED (single image, VALID or KEEP) and then every "5" in this
+ * header reads n: k holds n values, tap t acts at offset t-(n-1)/2, the
+ * VALID output is (H-n+1) x (W-n+1), the KEEP frame is (n-1)/2 pixels wide,
+ * and H, W >= n.  Batches, serving, the two-pass and direct forms, the
+ * offload and in-place calls are built for width 5.  tile_h/tile_w/stages: 0 = take the autotuned (or
  * built-in default) choice; otherwise one of the compiled fused-kernel shapes
  * (sepconv5_fused_configs).
  * Plane strides: 0 = planes stacked ([planes][H][pitch]: H*in_pitch for the
@@ -120,6 +126,7 @@ typedef struct {
     int32_t tile_h, tile_w, stages;
     int32_t ctas_per_sm;           /* 0 = as many as fit */
     int64_t in_plane_stride, out_plane_stride;
+    int32_t taps;                  /* kernel width: 0 or 5 (the paper's), or 3, 7, 9 */
 } sc5_plan_desc;
 
 typedef struct sc5_plan_s *sc5_plan;
@@ -150,8 +157,8 @@ SC5_API sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out);
 SC5_API sc5_status sepconv5_plan_destroy(sc5_plan plan);
 
 /* Run the plan on one image: in (dev, in_dtype, [planes][H][in_pitch]),
- * out (dev, out_dtype, layout per border), k (host, 5 taps, copied by
- * value).  in_scale > 0 and out_scale > 0 must be finite; the result code is
+ * out (dev, out_dtype, layout per border), k (host, the plan's taps values --
+ * 5 unless the plan says otherwise -- copied by value).  in_scale > 0 and out_scale > 0 must be finite; the result code is
  * round(B * out_scale) with B computed from value(in)/in_scale.  `in` and
  * `out` must not overlap.  Asynchronous on `stream`. */
 SC5_API sc5_status sepconv5_run(sc5_plan plan, const void *in, void *out, const float k[5],

@@ -112,10 +112,14 @@ static sc5_status encode_image_map(CUtensorMap *m, int dtype, const void *base, 
     return SC5_OK;
 }
 
-static int box_w_for(int dtype, int tile_w)
+// Columns of the TMA box: the tile plus the taps-1 halo, rounded up to 16
+// bytes and to the last lane's 4-element loads (as fused_box_w in the kernel).
+static int box_w_for(int dtype, int tile_w, int taps = kTaps)
 {
     const int es = dtype_bytes(dtype);
-    return ((tile_w + kHalo) * es + 15) / 16 * 16 / es;
+    const int row_elems = (taps + 6) / 4 * 4;
+    const int need = std::max(tile_w + taps - 1, tile_w - 4 + row_elems);
+    return (need * es + 15) / 16 * 16 / es;
 }
 
 // ------------------------------------------------------------------ validation
@@ -129,18 +133,21 @@ static bool planes_disjoint(int P, int64_t rows, int64_t width, int64_t pitch, i
 
 static sc5_status check_image(int in_dtype, int out_dtype, int border, const void *in, const void *out,
                               int P, int H, int W, int64_t in_pitch, int64_t out_pitch, float in_scale,
-                              float out_scale, bool need_ptrs, int64_t in_ps = 0, int64_t out_ps = 0)
+                              float out_scale, bool need_ptrs, int64_t in_ps = 0, int64_t out_ps = 0,
+                              int taps = kTaps)
 {
-    if (P < 1 || H < 5 || W < 5) return fail(SC5_EINVAL, "need planes >= 1, H >= 5, W >= 5 (got %d, %d, %d)", P, H, W);
+    if (P < 1 || H < taps || W < taps)
+        return fail(SC5_EINVAL, "need planes >= 1, H >= %d, W >= %d (got %d, %d, %d)", taps, taps, P, H, W);
+    const int halo = taps - 1;
     if (H > 65535 * 8 || W > (1 << 30)) return fail(SC5_EINVAL, "image too large (H <= 524280, W < 2^30)");
     const int ei = dtype_bytes(in_dtype), eo = dtype_bytes(out_dtype);
     if (!ei || !eo) return fail(SC5_EINVAL, "unknown dtype (%d, %d)", in_dtype, out_dtype);
     if (border != SC5_BORDER_VALID && border != SC5_BORDER_KEEP) return fail(SC5_EINVAL, "unknown border %d", border);
-    const int64_t wout = border == SC5_BORDER_KEEP ? W : W - kHalo;
+    const int64_t wout = border == SC5_BORDER_KEEP ? W : W - halo;
     if (in_pitch < W) return fail(SC5_EINVAL, "in_pitch %lld < W %d", (long long)in_pitch, W);
     if (out_pitch < wout) return fail(SC5_EINVAL, "out_pitch %lld < output width %lld", (long long)out_pitch, (long long)wout);
     if ((in_pitch * ei) % 16) return fail(SC5_EINVAL, "in_pitch * element size must be a multiple of 16 bytes");
-    const int64_t hout = border == SC5_BORDER_KEEP ? H : H - kHalo;
+    const int64_t hout = border == SC5_BORDER_KEEP ? H : H - halo;
     if (in_ps < 0 || out_ps < 0) return fail(SC5_EINVAL, "negative plane stride");
     if (in_ps == 0) in_ps = static_cast<int64_t>(H) * in_pitch;
     if (out_ps == 0) out_ps = hout * out_pitch;
@@ -176,9 +183,11 @@ static int64_t in_plane_of(const sc5_plan_desc &d)
     return d.in_plane_stride > 0 ? d.in_plane_stride : static_cast<int64_t>(d.H) * d.in_pitch;
 }
 
+static int taps_of(const sc5_plan_desc &d) { return d.taps > 0 ? d.taps : kTaps; }
+
 static int64_t out_plane_of(const sc5_plan_desc &d)
 {
-    const int64_t hout = d.border == SC5_BORDER_KEEP ? d.H : d.H - kHalo;
+    const int64_t hout = d.border == SC5_BORDER_KEEP ? d.H : d.H - (taps_of(d) - 1);
     return d.out_plane_stride > 0 ? d.out_plane_stride : hout * d.out_pitch;
 }
 
@@ -191,29 +200,31 @@ static bool default_strides(const sc5_plan_desc &d)
 static sc5_status fill_desc(ImgDesc *d, int in_dtype, int out_dtype, int border, const FusedShape &sh,
                             const void *in, void *out, int P, int H, int W, int64_t in_pitch,
                             int64_t out_pitch, const float *k, float in_scale, float out_scale,
-                            const float *K = nullptr, int64_t in_ps = 0, int64_t out_ps = 0)
+                            const float *K = nullptr, int64_t in_ps = 0, int64_t out_ps = 0, int taps = kTaps)
 {
     std::memset(d, 0, sizeof *d);
+    const int halo = taps - 1, radius = halo / 2;
     sc5_status st = encode_image_map(&d->tmap, in_dtype, in, P, H, W, in_pitch,
-                                     box_w_for(in_dtype, sh.tile_w), sh.tile_h + kHalo, in_ps);
+                                     box_w_for(in_dtype, sh.tile_w, taps), sh.tile_h + halo, in_ps);
     if (st != SC5_OK) return st;
     const int eo = dtype_bytes(out_dtype);
     char *ob = static_cast<char *>(out);
-    int64_t plane_rows = H - kHalo;
+    int64_t plane_rows = H - halo;
     if (border == SC5_BORDER_KEEP) {
-        ob += (2 * out_pitch + 2) * eo;
+        ob += (radius * out_pitch + radius) * eo;
         plane_rows = H;
     }
     d->out = ob;
     d->out_pitch = out_pitch;
     d->out_plane = out_ps > 0 ? out_ps : plane_rows * out_pitch;
-    d->Hv = H - kHalo;
-    d->Wv = W - kHalo;
+    d->Hv = H - halo;
+    d->Wv = W - halo;
     d->tiles_x = (d->Wv + sh.tile_w - 1) / sh.tile_w;
     d->tiles_y = (d->Hv + sh.tile_h - 1) / sh.tile_h;
-    for (int i = 0; i < kTaps; ++i) d->k[i] = k[i];
-    for (int i = 0; i < kTaps * kTaps; ++i)
-        d->K[i] = K ? K[i] : static_cast<float>(static_cast<double>(k[i / kTaps]) * k[i % kTaps]);
+    for (int i = 0; i < taps; ++i) d->k[i] = k[i];
+    if (taps == kTaps)
+        for (int i = 0; i < kTaps * kTaps; ++i)
+            d->K[i] = K ? K[i] : static_cast<float>(static_cast<double>(k[i / kTaps]) * k[i % kTaps]);
     d->oscale = static_cast<float>(static_cast<double>(out_scale) / static_cast<double>(in_scale));
     d->vec = (reinterpret_cast<uintptr_t>(ob) % (4 * eo) == 0 && out_pitch % 4 == 0) ? 1 : 0;
     return SC5_OK;
@@ -251,16 +262,16 @@ struct sc5_plan_s {
 
 namespace sc5 {
 sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
-                        bool direct)
+                        bool direct, int taps)
 {
     if (ov && (ov->tile_h || ov->tile_w || ov->stages)) {
         const int i = fused_find_shape(in_dtype, out_dtype, ov->tile_h ? ov->tile_h : 64,
-                                       ov->tile_w ? ov->tile_w : 128, ov->stages, direct);
+                                       ov->tile_w ? ov->tile_w : 128, ov->stages, direct, taps);
         if (i < 0) return fail(SC5_EINVAL, "no compiled fused shape %dx%d with %d stages for this dtype pair",
                                ov->tile_h, ov->tile_w, ov->stages);
         *idx = i;
         *ctas = ov->ctas_per_sm;
-    } else if (direct) {
+    } else if (direct || taps != kTaps) {
         *idx = 0;
         if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
     } else {
@@ -272,7 +283,7 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         if (*idx < 0) *idx = 0;
         if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
     }
-    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx, direct);
+    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx, direct, taps);
     if (maxc <= 0) return fail(SC5_ECUDA, "occupancy query failed for fused shape %d", *idx);
     if (*ctas <= 0 || *ctas > maxc) *ctas = maxc;
     return SC5_OK;
@@ -284,11 +295,17 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     clear_error();
     if (!desc || !out) return fail(SC5_EINVAL, "null argument");
     *out = nullptr;
-    const sc5_plan_desc &d = *desc;
+    sc5_plan_desc d = *desc;
+    if (d.taps == 0) d.taps = kTaps;
     if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS && d.algo != SC5_ALGO_DIRECT)
         return fail(SC5_EINVAL, "unknown algo %d", d.algo);
+    if (d.taps != 3 && d.taps != 5 && d.taps != 7 && d.taps != 9)
+        return fail(SC5_EINVAL, "taps must be 3, 5, 7 or 9 (got %d)", d.taps);
+    if (d.taps != kTaps && d.algo != SC5_ALGO_FUSED)
+        return fail(SC5_EINVAL, "widths other than 5 are built for the fused form only");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
-                                d.in_pitch, d.out_pitch, 1.f, 1.f, false, d.in_plane_stride, d.out_plane_stride);
+                                d.in_pitch, d.out_pitch, 1.f, 1.f, false, d.in_plane_stride, d.out_plane_stride,
+                                d.taps);
     if (st != SC5_OK) return st;
     if (!pair_supported(d.in_dtype, d.out_dtype))
         return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built: the output must be the input format or FP32",
@@ -299,12 +316,12 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     p->d = d;
     cudaGetDevice(&p->device);
     const bool direct = d.algo == SC5_ALGO_DIRECT;
-    st = choose_shape(d.in_dtype, d.out_dtype, d.H, d.W, &d, &p->shape_idx, &p->ctas_per_sm, direct);
+    st = choose_shape(d.in_dtype, d.out_dtype, d.H, d.W, &d, &p->shape_idx, &p->ctas_per_sm, direct, d.taps);
     if (st != SC5_OK) {
         delete p;
         return st;
     }
-    fused_shape(d.in_dtype, d.out_dtype, p->shape_idx, &p->shape, direct);
+    fused_shape(d.in_dtype, d.out_dtype, p->shape_idx, &p->shape, direct, d.taps);
     if (d.algo == SC5_ALGO_TWO_PASS) {
         p->t_pitch = (static_cast<int64_t>(d.W - kHalo) + 3) / 4 * 4;
         const size_t bytes = static_cast<size_t>(d.planes) * d.H * p->t_pitch * sizeof(float);
@@ -369,7 +386,7 @@ static sc5_status run_frame(const sc5_plan_desc &d, const void *in, void *out, f
     if (d.border != SC5_BORDER_KEEP) return SC5_OK;
     const float ratio = static_cast<float>(static_cast<double>(out_scale) / in_scale);
     cudaError_t e = launch_keep_frame(d.in_dtype, d.out_dtype, in, d.planes, d.H, d.W, d.in_pitch, out,
-                                      d.out_pitch, ratio, st, in_plane_of(d), out_plane_of(d));
+                                      d.out_pitch, ratio, st, in_plane_of(d), out_plane_of(d), (taps_of(d) - 1) / 2);
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "frame launch");
 }
 
@@ -381,14 +398,14 @@ static sc5_status run_single_pass(sc5_plan p, const void *in, void *out, const f
     ImgDesc desc;
     sc5_status st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, in, out, d.planes, d.H, d.W,
                               d.in_pitch, d.out_pitch, k, in_scale, out_scale, K, d.in_plane_stride,
-                              d.out_plane_stride);
+                              d.out_plane_stride, taps_of(d));
     if (desc.out_plane % 4) desc.vec = 0;
     if (st != SC5_OK) return st;
     const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
     const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
     const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, cap)));
     cudaError_t e = launch_fused_single(d.in_dtype, d.out_dtype, p->shape_idx, desc, ntiles, grid, s,
-                                        d.algo == SC5_ALGO_DIRECT);
+                                        d.algo == SC5_ALGO_DIRECT, taps_of(d));
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "single-pass launch");
 }
 
@@ -399,9 +416,11 @@ extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const 
     if (!p || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
-                                d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride);
+                                d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride,
+                                taps_of(d));
     if (st != SC5_OK) return st;
-    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    for (int t = 0; t < taps_of(d); ++t)
+        if (!std::isfinite(k[t])) return fail(SC5_EINVAL, "taps must be finite");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (d.algo == SC5_ALGO_TWO_PASS) {
         st = run_two_pass(p, in, out, k, in_scale, out_scale, s);
@@ -439,6 +458,7 @@ extern "C" sc5_status sepconv5_run_inplace(sc5_plan p, void *img, const float k[
     if (d.in_dtype != d.out_dtype || d.border != SC5_BORDER_KEEP || d.out_pitch != d.in_pitch)
         return fail(SC5_EINVAL, "in-place needs in_dtype == out_dtype, border KEEP and out_pitch == in_pitch");
     if (!default_strides(d)) return fail(SC5_EINVAL, "in-place takes stacked planes (plane strides 0)");
+    if (taps_of(d) != kTaps) return fail(SC5_EINVAL, "in-place is built for width 5");
     if (reinterpret_cast<uintptr_t>(img) % 16) return fail(SC5_EINVAL, "image must be 16-byte aligned");
     if (!(scale > 0.f) || !std::isfinite(scale)) return fail(SC5_EINVAL, "scale must be finite and > 0");
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
@@ -480,6 +500,7 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
     if (!p || !host_in || !host_out || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
     if (!default_strides(d)) return fail(SC5_EINVAL, "the offload call takes stacked planes (plane strides 0)");
+    if (taps_of(d) != kTaps) return fail(SC5_EINVAL, "the offload call is built for width 5");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, false);
     if (st != SC5_OK) return st;
@@ -688,6 +709,7 @@ extern "C" sc5_status sepconv5_run_batch(sc5_plan p, int32_t n, const sc5_image 
     clear_error();
     if (!p) return fail(SC5_EINVAL, "null plan");
     if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
+    if (taps_of(p->d) != kTaps) return fail(SC5_EINVAL, "batches are built for width 5");
     int idx = 0, ctas = 1;
     sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
     if (st != SC5_OK) return st;
@@ -761,6 +783,7 @@ extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_ima
     if (!p || !out) return fail(SC5_EINVAL, "null argument");
     *out = nullptr;
     if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
+    if (taps_of(p->d) != kTaps) return fail(SC5_EINVAL, "batches are built for width 5");
     int idx = 0, ctas = 1;
     sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
     if (st != SC5_OK) return st;

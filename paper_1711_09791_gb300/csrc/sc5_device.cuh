@@ -163,12 +163,15 @@ template <class T> struct Fmt;
 template <> struct Fmt<float> {
     static constexpr int bytes = 4;
     static constexpr bool kStride2 = false;
-    __device__ static __forceinline__ void load8(const float *p, float (&a)[8])
+    __device__ static __forceinline__ void load4(const float *p, float *a)
     {
         const float4 u = *reinterpret_cast<const float4 *>(p);
-        const float4 v = *reinterpret_cast<const float4 *>(p + 4);
         a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
-        a[4] = v.x; a[5] = v.y; a[6] = v.z; a[7] = v.w;
+    }
+    __device__ static __forceinline__ void load8(const float *p, float (&a)[8])
+    {
+        load4(p, a);
+        load4(p + 4, a + 4);
     }
     __device__ static __forceinline__ float load1(const float *p) { return *p; }
     __device__ static __forceinline__ void store4(float *p, const float (&r)[4])
@@ -183,13 +186,15 @@ template <> struct Fmt<bf16_t> {
     static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const bf16_t *p, float (&a)[8])
     {
+        load4(p, a);
+        load4(p + 4, a + 4);
+    }
+    __device__ static __forceinline__ void load4(const bf16_t *p, float *a)
+    {
         // a bfloat16 is the upper half of a binary32: one shift or mask per element
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
-        const uint2 v = *reinterpret_cast<const uint2 *>(p + 4);
         a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xffff0000u);
         a[2] = __uint_as_float(u.y << 16); a[3] = __uint_as_float(u.y & 0xffff0000u);
-        a[4] = __uint_as_float(v.x << 16); a[5] = __uint_as_float(v.x & 0xffff0000u);
-        a[6] = __uint_as_float(v.y << 16); a[7] = __uint_as_float(v.y & 0xffff0000u);
     }
     __device__ static __forceinline__ float load1(const bf16_t *p) { return bf16_bits_to_f32(p->v); }
     __device__ static __forceinline__ void store4(bf16_t *p, const float (&r)[4])
@@ -210,12 +215,14 @@ template <> struct Fmt<f16_t> {
     static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const f16_t *p, float (&a)[8])
     {
+        load4(p, a);
+        load4(p + 4, a + 4);
+    }
+    __device__ static __forceinline__ void load4(const f16_t *p, float *a)
+    {
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
-        const uint2 v = *reinterpret_cast<const uint2 *>(p + 4);
         f16x2_to_f32(u.x, a[0], a[1]);
         f16x2_to_f32(u.y, a[2], a[3]);
-        f16x2_to_f32(v.x, a[4], a[5]);
-        f16x2_to_f32(v.y, a[6], a[7]);
     }
     __device__ static __forceinline__ float load1(const f16_t *p)
     {
@@ -241,12 +248,14 @@ template <> struct Fmt<fp8e4m3_t> {
     static constexpr bool kStride2 = true;
     __device__ static __forceinline__ void load8(const fp8e4m3_t *p, float (&a)[8])
     {
+        load4(p, a);
+        load4(p + 4, a + 4);
+    }
+    __device__ static __forceinline__ void load4(const fp8e4m3_t *p, float *a)
+    {
         const uint32_t u = *reinterpret_cast<const uint32_t *>(p);
-        const uint32_t v = *reinterpret_cast<const uint32_t *>(p + 4);
         e4m3x2_to_f32(u & 0xffffu, a[0], a[1]);
         e4m3x2_to_f32(u >> 16, a[2], a[3]);
-        e4m3x2_to_f32(v & 0xffffu, a[4], a[5]);
-        e4m3x2_to_f32(v >> 16, a[6], a[7]);
     }
     __device__ static __forceinline__ float load1(const fp8e4m3_t *p)
     {

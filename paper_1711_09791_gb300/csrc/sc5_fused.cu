@@ -14,13 +14,26 @@ int fused_entries_fp8(int out_dtype, const FusedEntry **out);
 int fused_direct_entries_f32(int out_dtype, const FusedEntry **out);
 int fused_direct_entries_16(int in_dtype, int out_dtype, const FusedEntry **out);
 int fused_direct_entries_fp8(int out_dtype, const FusedEntry **out);
+int fused_width_entries_f32(int out_dtype, int taps, const FusedEntry **out);
+int fused_width_entries_16(int in_dtype, int out_dtype, int taps, const FusedEntry **out);
+int fused_width_entries_fp8(int out_dtype, int taps, const FusedEntry **out);
 
 // Device status word: 0 = no error; a kernel whose bounded wait ran out
 // writes its error code here (first writer wins).
 __device__ int g_status;
 
-static int entries(int in_dtype, int out_dtype, const FusedEntry **e, bool direct = false)
+static int entries(int in_dtype, int out_dtype, const FusedEntry **e, bool direct = false, int taps = kTaps)
 {
+    if (taps != kTaps) {
+        if (direct) return 0;
+        switch (in_dtype) {
+        case SC5_F32: return fused_width_entries_f32(out_dtype, taps, e);
+        case SC5_BF16:
+        case SC5_F16: return fused_width_entries_16(in_dtype, out_dtype, taps, e);
+        case SC5_FP8E4M3: return fused_width_entries_fp8(out_dtype, taps, e);
+        default: return 0;
+        }
+    }
     switch (in_dtype) {
     case SC5_F32: return direct ? fused_direct_entries_f32(out_dtype, e) : fused_entries_f32(out_dtype, e);
     case SC5_BF16:
@@ -31,25 +44,25 @@ static int entries(int in_dtype, int out_dtype, const FusedEntry **e, bool direc
     }
 }
 
-int fused_num_shapes(int in_dtype, int out_dtype, bool direct)
+int fused_num_shapes(int in_dtype, int out_dtype, bool direct, int taps)
 {
     const FusedEntry *e;
-    return entries(in_dtype, out_dtype, &e, direct);
+    return entries(in_dtype, out_dtype, &e, direct, taps);
 }
 
-bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct)
+bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct, int taps)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e, direct);
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
     if (idx < 0 || idx >= n) return false;
     *s = e[idx].shape;
     return true;
 }
 
-int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct)
+int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct, int taps)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e, direct);
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
     for (int i = 0; i < n; ++i)
         if (e[i].shape.tile_h == tile_h && e[i].shape.tile_w == tile_w &&
             (stages == 0 || e[i].shape.stages == stages))
@@ -58,14 +71,6 @@ int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int st
 }
 
 int fused_threads(const FusedShape &s) { return 32 * (s.tile_h / s.rows_per_thread + 1); }
-
-int fused_smem_bytes(int in_dtype, const FusedShape &s)
-{
-    const int es = dtype_bytes(in_dtype);
-    const int bw = ((s.tile_w + kHalo) * es + 15) / 16 * 16 / es;
-    const int stage = (bw * (s.tile_h + kHalo) * es + 127) / 128 * 128;
-    return s.stages * stage;
-}
 
 // cudaFuncSetAttribute for the dynamic shared memory once per (function, device).
 static cudaError_t prepare_fn(const void *fn, int smem)
@@ -97,10 +102,10 @@ static int *status_ptr()
     return ptrs[dev];
 }
 
-int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct)
+int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct, int taps)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e, direct);
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
     if (idx < 0 || idx >= n) return -1;
     if (prepare_fn(e[idx].single_fn, e[idx].smem) != cudaSuccess) return -1;
     int blocks = 0;
@@ -110,10 +115,10 @@ int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct)
     return blocks;
 }
 
-cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct)
+cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct, int taps)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e, direct);
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
     if (idx < 0 || idx >= n) return cudaErrorInvalidValue;
     cudaError_t err = prepare_fn(e[idx].single_fn, e[idx].smem);
     if (err == cudaSuccess) err = prepare_fn(e[idx].batch_fn, e[idx].smem);
@@ -122,13 +127,13 @@ cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct)
 }
 
 cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgDesc &d,
-                                int64_t ntiles, int grid, cudaStream_t st, bool direct)
+                                int64_t ntiles, int grid, cudaStream_t st, bool direct, int taps)
 {
     const FusedEntry *e;
-    const int n = entries(in_dtype, out_dtype, &e, direct);
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
     if (idx < 0 || idx >= n || grid < 1) return cudaErrorInvalidValue;
     if (ntiles <= 0) return cudaSuccess;
-    cudaError_t err = fused_prepare(in_dtype, out_dtype, idx, direct);
+    cudaError_t err = fused_prepare(in_dtype, out_dtype, idx, direct, taps);
     if (err != cudaSuccess) return err;
     int *status = status_ptr();
     const ImgDesc *no_descs = nullptr;

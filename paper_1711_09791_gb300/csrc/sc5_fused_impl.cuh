@@ -30,17 +30,28 @@ namespace sc5 {
 constexpr uint64_t kWaitLimitNs = 1000ull * 1000ull * 1000ull;  // 1 s per wait
 constexpr uint64_t kDrainLimitNs = 100ull * 1000ull * 1000ull;  // 0.1 s after an error
 
-template <class TIn>
-__host__ __device__ constexpr int fused_box_w(int tw)
+// Elements of one input row a lane widens: its 4 columns plus the TAPS-1
+// halo, rounded up to whole 4-element loads.
+template <int TAPS>
+__host__ __device__ constexpr int row_elems()
 {
-    // TW + 4 columns rounded up so that a box row is a multiple of 16 bytes
-    return ((tw + kHalo) * Fmt<TIn>::bytes + 15) / 16 * 16 / Fmt<TIn>::bytes;
+    return (TAPS + 3 + 3) / 4 * 4;
 }
 
-template <class TIn, int TH, int TW>
+template <class TIn, int TAPS = kTaps>
+__host__ __device__ constexpr int fused_box_w(int tw)
+{
+    // TW + TAPS - 1 columns rounded up so that a box row is a multiple of 16
+    // bytes, and wide enough for the last lane's loads
+    constexpr int es = Fmt<TIn>::bytes;
+    const int need = (tw + TAPS - 1) > (tw - 4 + row_elems<TAPS>()) ? (tw + TAPS - 1) : (tw - 4 + row_elems<TAPS>());
+    return (need * es + 15) / 16 * 16 / es;
+}
+
+template <class TIn, int TH, int TW, int TAPS = kTaps>
 __host__ __device__ constexpr int fused_stage_bytes()
 {
-    return (fused_box_w<TIn>(TW) * (TH + kHalo) * Fmt<TIn>::bytes + 127) / 128 * 128;
+    return (fused_box_w<TIn, TAPS>(TW) * (TH + TAPS - 1) * Fmt<TIn>::bytes + 127) / 128 * 128;
 }
 
 // The input pairs of one row for the packed arithmetic.  Output columns are
@@ -50,26 +61,34 @@ __host__ __device__ constexpr int fused_stage_bytes()
 // 16-byte loads already fill, odd j the shifted pairs.  Narrow formats use
 // column pairs (0,2) and (1,3): PL[j] = (a[j], a[j+2]), PR[j] = (a[j+1], a[j+3]),
 // each half widened straight into its slot.
-template <class TIn>
-__device__ __forceinline__ void row_pairs(const TIn *__restrict__ p, uint64_t (&PL)[kTaps], uint64_t (&PR)[kTaps])
+template <class TIn, int TAPS = kTaps>
+__device__ __forceinline__ void row_pairs(const TIn *__restrict__ p, uint64_t (&PL)[TAPS], uint64_t (&PR)[TAPS])
 {
-    float a[8];
-    Fmt<TIn>::load8(p, a);
+    constexpr int NE = row_elems<TAPS>();
+    float a[NE];
+#pragma unroll
+    for (int q = 0; q < NE; q += 4) Fmt<TIn>::load4(p + q, a + q);
     if constexpr (Fmt<TIn>::kStride2) {
-        uint64_t S[6];
+        uint64_t S[TAPS + 1];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) S[j] = pack2(a[j], a[j + 2]);
+        for (int j = 0; j <= TAPS; ++j) S[j] = pack2(a[j], a[j + 2]);
 #pragma unroll
-        for (int j = 0; j < kTaps; ++j) {
+        for (int j = 0; j < TAPS; ++j) {
             PL[j] = S[j];
             PR[j] = S[j + 1];
         }
     } else {
-        const uint64_t E0 = pack2(a[0], a[1]), E1 = pack2(a[2], a[3]);
-        const uint64_t E2 = pack2(a[4], a[5]), E3 = pack2(a[6], a[7]);
-        const uint64_t O0 = pack2(a[1], a[2]), O1 = pack2(a[3], a[4]), O2 = pack2(a[5], a[6]);
-        PL[0] = E0; PL[1] = O0; PL[2] = E1; PL[3] = O1; PL[4] = E2;
-        PR[0] = E1; PR[1] = O1; PR[2] = E2; PR[3] = O2; PR[4] = E3;
+        // E[m] = (a[2m], a[2m+1]) and O[m] = (a[2m+1], a[2m+2])
+        uint64_t E[(TAPS + 4) / 2], O[(TAPS + 2) / 2];
+#pragma unroll
+        for (int m = 0; m < (TAPS + 4) / 2; ++m) E[m] = pack2(a[2 * m], a[2 * m + 1]);
+#pragma unroll
+        for (int m = 0; m < (TAPS + 2) / 2; ++m) O[m] = pack2(a[2 * m + 1], a[2 * m + 2]);
+#pragma unroll
+        for (int j = 0; j < TAPS; ++j) {
+            PL[j] = (j % 2 == 0) ? E[j / 2] : O[j / 2];            // (a[j], a[j+1])
+            PR[j] = (j % 2 == 0) ? E[j / 2 + 1] : O[j / 2 + 1];    // (a[j+2], a[j+3])
+        }
     }
 }
 
@@ -105,33 +124,33 @@ __device__ __forceinline__ void store_row(uint64_t vL, uint64_t vR, uint64_t os2
 //   kk:  the taps as pairs (k[t], k[t]); os2 = (oscale, oscale)
 // Per element this is exactly hdot's sequence for the row pass (k0*a0, then
 // fused multiply-adds for t = 1..4), and the same sequence down the column.
-template <class TIn, class TOut, int R, int BW>
-__device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps],
+template <class TIn, class TOut, int R, int BW, int TAPS = kTaps>
+__device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[TAPS],
                                            uint64_t os2, bool scaled, TOut *__restrict__ out,
                                            int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
 {
     uint64_t accL[R], accR[R];
 #pragma unroll
-    for (int r = 0; r < R + kHalo; ++r) {
-        uint64_t PL[kTaps], PR[kTaps];
-        row_pairs<TIn>(s + r * BW, PL, PR);
+    for (int r = 0; r < R + TAPS - 1; ++r) {
+        uint64_t PL[TAPS], PR[TAPS];
+        row_pairs<TIn, TAPS>(s + r * BW, PL, PR);
         uint64_t hL = mul2(kk[0], PL[0]);
         uint64_t hR = mul2(kk[0], PR[0]);
 #pragma unroll
-        for (int t = 1; t < kTaps; ++t) {
+        for (int t = 1; t < TAPS; ++t) {
             hL = fma2(kk[t], PL[t], hL);
             hR = fma2(kk[t], PR[t], hR);
         }
         // input row r carries tap t = r - o of output row o
 #pragma unroll
-        for (int t = 0; t < kTaps; ++t) {
+        for (int t = 0; t < TAPS; ++t) {
             const int o = r - t;
             if (o >= 0 && o < R) {
                 accL[o] = (t == 0) ? mul2(kk[0], hL) : fma2(kk[t], hL, accL[o]);
                 accR[o] = (t == 0) ? mul2(kk[0], hR) : fma2(kk[t], hR, accR[o]);
             }
         }
-        const int o = r - kHalo;  // output row o has all five taps now
+        const int o = r - (TAPS - 1);  // output row o has all its taps now
         if (o >= 0 && o < rows_valid)
             store_row<TIn, TOut>(accL[o], accR[o], os2, scaled, out + static_cast<int64_t>(o) * out_pitch,
                                  cols_valid, vec);
@@ -182,17 +201,19 @@ __device__ __forceinline__ void record_error(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
-template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH, bool DIRECT = false>
+template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH, bool DIRECT = false, int TAPS = kTaps>
 __global__ void __launch_bounds__(32 * (TH / R + 1), 1)
 fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__ descs,
              const TileRec *__restrict__ tiles, int64_t ntiles, int *status)
 {
     static_assert(TW == 32 * kColsPerThread, "one warp spans the tile width");
     static_assert(TH % R == 0, "rows per thread must divide the tile height");
+    static_assert(TAPS % 2 == 1 && TAPS <= kMaxTaps, "odd width up to kMaxTaps");
+    static_assert(!DIRECT || TAPS == kTaps, "the direct form is built for width 5");
     constexpr int NC = TH / R;                       // consumer warps
-    constexpr int BW = fused_box_w<TIn>(TW);
-    constexpr int STAGE = fused_stage_bytes<TIn, TH, TW>();
-    constexpr uint32_t TX = BW * (TH + kHalo) * Fmt<TIn>::bytes;
+    constexpr int BW = fused_box_w<TIn, TAPS>(TW);
+    constexpr int STAGE = fused_stage_bytes<TIn, TH, TW, TAPS>();
+    constexpr uint32_t TX = BW * (TH + TAPS - 1) * Fmt<TIn>::bytes;
 
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S];
@@ -252,7 +273,7 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
 
     // ---------------------------------------------------------------- consumers
     // Per-image fields in registers: once for a single image, per tile in a batch.
-    uint64_t kk[kTaps];
+    uint64_t kk[TAPS];
     uint64_t KK[DIRECT ? kTaps * kTaps : 1];
     uint64_t os2 = 0;
     bool scaled = false;
@@ -266,7 +287,7 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             for (int q = 0; q < kTaps * kTaps; ++q) KK[q] = pack2(d.K[q], d.K[q]);
         } else {
 #pragma unroll
-            for (int q = 0; q < kTaps; ++q) kk[q] = pack2(d.k[q], d.k[q]);
+            for (int q = 0; q < TAPS; ++q) kk[q] = pack2(d.k[q], d.k[q]);
         }
         os2 = pack2(d.oscale, d.oscale);
         scaled = d.oscale != 1.f;  // multiplying by exactly 1 would change nothing
@@ -302,7 +323,7 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             if constexpr (DIRECT)
                 conv_strip_direct<TIn, TOut, R, BW>(src, KK, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
             else
-                conv_strip<TIn, TOut, R, BW>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
+                conv_strip<TIn, TOut, R, BW, TAPS>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -319,14 +340,14 @@ struct FusedEntry {
     int threads;
 };
 
-template <class TIn, class TOut, int TH, int TW, int R, int S, bool DIRECT = false>
+template <class TIn, class TOut, int TH, int TW, int R, int S, bool DIRECT = false, int TAPS = kTaps>
 FusedEntry make_entry()
 {
     FusedEntry e;
     e.shape = FusedShape{TH, TW, R, S};
-    e.single_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, false, DIRECT>);
-    e.batch_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, true, DIRECT>);
-    e.smem = S * fused_stage_bytes<TIn, TH, TW>();
+    e.single_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, false, DIRECT, TAPS>);
+    e.batch_fn = reinterpret_cast<const void *>(&fused_kernel<TIn, TOut, TH, TW, R, S, true, DIRECT, TAPS>);
+    e.smem = S * fused_stage_bytes<TIn, TH, TW, TAPS>();
     e.threads = 32 * (TH / R + 1);
     return e;
 }

@@ -14,6 +14,7 @@ namespace sc5 {
 
 constexpr int kTaps = 5;
 constexpr int kHalo = 4;          // a width-5 kernel needs 2 extra pixels per side
+constexpr int kMaxTaps = 9;       // widest kernel the fused separable path is built for
 constexpr int kColsPerThread = 4; // output columns per consumer thread
 
 // Error codes written to the device status word.
@@ -28,11 +29,11 @@ struct alignas(64) ImgDesc {
     int64_t out_plane;     // elements between planes
     int32_t Hv, Wv;        // VALID output rows / cols
     int32_t tiles_x, tiles_y;
-    float k[kTaps];
+    float k[kMaxTaps];     // taps (the first `taps` entries are used)
     float oscale;          // out_scale / in_scale
     int32_t vec;           // 1: 4-wide vector stores are aligned
     float K[kTaps * kTaps];  // direct form: the 5x5 matrix, row-major, K[i][j] at offset (i-2, j-2)
-    int32_t pad_[12];
+    int32_t pad_[8];
 };
 static_assert(sizeof(ImgDesc) % 64 == 0, "ImgDesc must keep the tensor map 64-byte aligned");
 
@@ -49,19 +50,21 @@ struct FusedShape {
 // Fused kernel launchers (sc5_fused.cu).  Return a cudaError_t.  `direct`
 // selects the direct single-pass kernels (25 products per output, K from the
 // descriptor); they have their own shape list.
-int fused_num_shapes(int in_dtype, int out_dtype, bool direct = false);
-bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct = false);
-int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct = false);
-// Bytes of dynamic shared memory and threads per CTA of a shape.
-int fused_smem_bytes(int in_dtype, const FusedShape &s);
+// `taps` (3, 5, 7 or 9) selects the separable kernels of that width (5 for
+// the direct kernels).
+int fused_num_shapes(int in_dtype, int out_dtype, bool direct = false, int taps = 5);
+bool fused_shape(int in_dtype, int out_dtype, int idx, FusedShape *s, bool direct = false, int taps = 5);
+int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int stages, bool direct = false,
+                     int taps = 5);
+// Threads per CTA of a shape.
 int fused_threads(const FusedShape &s);
 // Max resident CTAs per SM for a shape (occupancy query), or <= 0 on error.
-int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct = false);
+int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct = false, int taps = 5);
 // Set the kernel attributes of a shape on the current device (call before
 // capturing a launch into a graph).
-cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct = false);
+cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct = false, int taps = 5);
 cudaError_t launch_fused_single(int in_dtype, int out_dtype, int idx, const ImgDesc &d,
-                                int64_t ntiles, int grid, cudaStream_t st, bool direct = false);
+                                int64_t ntiles, int grid, cudaStream_t st, bool direct = false, int taps = 5);
 cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDesc *descs,
                                const TileRec *tiles, int64_t ntiles, int grid, cudaStream_t st);
 cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code);
@@ -75,7 +78,7 @@ cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, in
                          float oscale, bool vec, cudaStream_t st);
 cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
                               int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
-                              cudaStream_t st, int64_t in_plane = 0, int64_t out_plane = 0);
+                              cudaStream_t st, int64_t in_plane = 0, int64_t out_plane = 0, int radius = 2);
 cudaError_t launch_empty(int n, cudaStream_t st);
 // Copy a VALID image into an interior that starts 2 elements into its rows
 // (src rows 16-byte aligned, dst interior 2*element-size aligned).
@@ -91,7 +94,7 @@ sc5_status fail_cuda(cudaError_t e, const char *what);
 void clear_error();
 // Fused shape and CTAs/SM for a plane size (override > tuned table > default).
 sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
-                        bool direct = false);
+                        bool direct = false, int taps = kTaps);
 // Shape for a set of images: tuned choice for the size class with most pixels.
 sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas);
 // Host image of a batch launch: ImgDesc[n] then (256-byte aligned) TileRec[tiles].

@@ -109,23 +109,23 @@ vpass_kernel(const float *__restrict__ T, int H, int Wv, int64_t t_pitch, TOut *
 // in the output format (an exact copy when formats and scales agree).
 template <class TIn, class TOut>
 __global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t in_plane,
-                                  TOut *__restrict__ out, int64_t out_pitch, int64_t out_plane, float ratio)
+                                  TOut *__restrict__ out, int64_t out_pitch, int64_t out_plane, float ratio, int rad)
 {
-    const int64_t n_rows = 4ll * W;                 // rows 0, 1, H-2, H-1
-    const int64_t n = n_rows + 4ll * (H - kHalo);   // plus cols 0, 1, W-2, W-1 of rows 2..H-3
+    const int64_t n_rows = 2ll * rad * W;                    // rows 0..rad-1 and H-rad..H-1
+    const int64_t n = n_rows + 2ll * rad * (H - 2 * rad);    // plus the first and last rad columns between
     const int p = blockIdx.y;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         int y, x;
         if (i < n_rows) {
             const int r = static_cast<int>(i / W);
-            y = (r < 2) ? r : H - 4 + r;
+            y = (r < rad) ? r : H - 2 * rad + r;
             x = static_cast<int>(i % W);
         } else {
             const int64_t j = i - n_rows;
-            y = 2 + static_cast<int>(j / 4);
-            const int c = static_cast<int>(j % 4);
-            x = (c < 2) ? c : W - 4 + c;
+            y = rad + static_cast<int>(j / (2 * rad));
+            const int c = static_cast<int>(j % (2 * rad));
+            x = (c < rad) ? c : W - 2 * rad + c;
         }
         const float v = Fmt<TIn>::load1(in + p * in_plane + static_cast<int64_t>(y) * in_pitch + x);
         Fmt<TOut>::store1(out + p * out_plane + static_cast<int64_t>(y) * out_pitch + x, __fmul_rn(v, ratio));
@@ -252,15 +252,15 @@ cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, in
 
 template <class TIn>
 static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, int64_t in_pitch, int64_t in_plane,
-                             void *out, int64_t out_pitch, int64_t out_plane, float ratio, cudaStream_t st)
+                             void *out, int64_t out_pitch, int64_t out_plane, float ratio, cudaStream_t st, int rad)
 {
-    const int64_t n = 4ll * W + 4ll * (H - kHalo);
+    const int64_t n = 2ll * rad * W + 2ll * rad * (H - 2 * rad);
     const dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), P);
     switch (out_dtype) {
-    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<float *>(out), out_pitch, out_plane, ratio); break;
-    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<bf16_t *>(out), out_pitch, out_plane, ratio); break;
-    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<f16_t *>(out), out_pitch, out_plane, ratio); break;
-    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, ratio); break;
+    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<float *>(out), out_pitch, out_plane, ratio, rad); break;
+    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<bf16_t *>(out), out_pitch, out_plane, ratio, rad); break;
+    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<f16_t *>(out), out_pitch, out_plane, ratio, rad); break;
+    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, ratio, rad); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -268,16 +268,16 @@ static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, 
 
 cudaError_t launch_keep_frame(int in_dtype, int out_dtype, const void *in, int P, int H, int W,
                               int64_t in_pitch, void *out, int64_t out_pitch, float ratio,
-                              cudaStream_t st, int64_t in_plane, int64_t out_plane)
+                              cudaStream_t st, int64_t in_plane, int64_t out_plane, int rad)
 {
     if (in_plane <= 0) in_plane = static_cast<int64_t>(H) * in_pitch;
     if (out_plane <= 0) out_plane = static_cast<int64_t>(H) * out_pitch;
     cudaError_t err;
     switch (in_dtype) {
-    case SC5_F32: err = frame_out(out_dtype, static_cast<const float *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
-    case SC5_BF16: err = frame_out(out_dtype, static_cast<const bf16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
-    case SC5_F16: err = frame_out(out_dtype, static_cast<const f16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
-    case SC5_FP8E4M3: err = frame_out(out_dtype, static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st); break;
+    case SC5_F32: err = frame_out(out_dtype, static_cast<const float *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st, rad); break;
+    case SC5_BF16: err = frame_out(out_dtype, static_cast<const bf16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st, rad); break;
+    case SC5_F16: err = frame_out(out_dtype, static_cast<const f16_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st, rad); break;
+    case SC5_FP8E4M3: err = frame_out(out_dtype, static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, in_plane, out, out_pitch, out_plane, ratio, st, rad); break;
     default: return cudaErrorInvalidValue;
     }
     if (err == cudaSuccess) note_launches(1);

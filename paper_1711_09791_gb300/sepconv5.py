@@ -37,7 +37,7 @@ class PlanDesc(ctypes.Structure):
                 ("in_pitch", c_int64), ("out_pitch", c_int64),
                 ("in_dtype", c_int32), ("out_dtype", c_int32), ("border", c_int32), ("algo", c_int32),
                 ("tile_h", c_int32), ("tile_w", c_int32), ("stages", c_int32), ("ctas_per_sm", c_int32),
-                ("in_plane_stride", c_int64), ("out_plane_stride", c_int64)]
+                ("in_plane_stride", c_int64), ("out_plane_stride", c_int64), ("taps", c_int32)]
 
 
 class Image(ctypes.Structure):
@@ -138,11 +138,11 @@ def _stream(s) -> int | None:
     return int(s)
 
 
-def _taps(k):
+def _taps(k, n=5):
     vals = [float(v) for v in k]
-    if len(vals) != 5:
-        raise ValueError("k needs 5 taps")
-    return (c_float * 5)(*vals)
+    if len(vals) != n:
+        raise ValueError(f"k needs {n} taps")
+    return (c_float * n)(*vals)
 
 
 def _dt(d):
@@ -154,7 +154,7 @@ class Plan:
 
     def __init__(self, planes: int, H: int, W: int, in_pitch: int | None = None, out_pitch: int | None = None,
                  in_dtype="f32", out_dtype=None, border="valid", algo="fused", tile_h=0, tile_w=0, stages=0,
-                 ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0):
+                 ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0, taps=5):
         out_dtype = in_dtype if out_dtype is None else out_dtype
         b = BORDERS[border] if isinstance(border, str) else int(border)
         d = PlanDesc()
@@ -166,6 +166,11 @@ class Plan:
         d.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
         d.tile_h, d.tile_w, d.stages, d.ctas_per_sm = tile_h, tile_w, stages, ctas_per_sm
         d.in_plane_stride, d.out_plane_stride = in_plane_stride, out_plane_stride
+        d.taps = taps
+        self.taps = taps
+        halo = taps - 1
+        if out_pitch is None:
+            d.out_pitch = W if b == 1 else W - halo
         self.desc = d
         h = c_void_p()
         _check(load().sepconv5_plan(byref(d), byref(h)), "sepconv5_plan")
@@ -176,7 +181,7 @@ class Plan:
         return self._h
 
     def run(self, src, dst, k, in_scale=1.0, out_scale=1.0, stream=None):
-        _check(load().sepconv5_run(self._h, _ptr(src), _ptr(dst), _taps(k), in_scale, out_scale,
+        _check(load().sepconv5_run(self._h, _ptr(src), _ptr(dst), _taps(k, self.taps), in_scale, out_scale,
                                    _stream(stream)), "sepconv5_run")
 
     def run_K(self, src, dst, K, in_scale=1.0, out_scale=1.0, stream=None):
