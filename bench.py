@@ -536,6 +536,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         del X, Y
         extras["layout_3RxC"] = {"ms_per_step": round(msl, 5), "frac_of_measured_hbm": round(alg / (msl / 1e3) / 1e9 / peak, 4),
                                  "vs_stacked": round(msl / ms, 3)}
+        # other odd kernel widths through the fused kernel
+        widths = {}
+        for n in (3, 7, 9):
+            kn = synth.rng(100 + n).uniform(0, 1, n)
+            kn = (kn / kn.sum()).astype(np.float32)
+            outn = torch.empty((P, H - n + 1, W - n + 1), dtype=torch.float32, device=dev)
+            pl = sepconv5.Plan(P, H, W, W, W - n + 1, taps=n)
+            msn, _ = timed(lambda: pl.run(A_dev, outn, kn, stream=stream), k2, 3)
+            pl.close()
+            algn = P * H * W * 4 + P * (H - n + 1) * (W - n + 1) * 4
+            widths[f"taps_{n}"] = {"ms_per_step": round(msn, 5),
+                                   "frac_of_measured_hbm": round(algn / (msn / 1e3) / 1e9 / peak, 4)}
+            del outn
+        extras["widths"] = widths
         # in place: Listing 1's two-pass structure vs the single pass with copy-back
         A_ip = A_dev.clone()
         ip = {}

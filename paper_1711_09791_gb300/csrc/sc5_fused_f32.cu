@@ -20,29 +20,4 @@ int fused_entries_f32(int out_dtype, const FusedEntry **out)
     return 0;
 }
 
-int fused_direct_entries_f32(int out_dtype, const FusedEntry **out)
-{
-    static const FusedEntry f32_f32[] = {
-        make_entry<float, float, 64, 128, 4, 3, true>(),
-        make_entry<float, float, 32, 128, 2, 4, true>(),
-    };
-    if (out_dtype == SC5_F32) { *out = f32_f32; return static_cast<int>(sizeof f32_f32 / sizeof f32_f32[0]); }
-    return 0;
-}
-
-// Other odd widths (3, 7, 9) of the separable kernel: one shape each.
-int fused_width_entries_f32(int out_dtype, int taps, const FusedEntry **out)
-{
-    static const FusedEntry w3[] = {make_entry<float, float, 64, 128, 4, 3, false, 3>()};
-    static const FusedEntry w7[] = {make_entry<float, float, 64, 128, 4, 3, false, 7>()};
-    static const FusedEntry w9[] = {make_entry<float, float, 64, 128, 4, 3, false, 9>()};
-    if (out_dtype != SC5_F32) return 0;
-    switch (taps) {
-    case 3: *out = w3; return 1;
-    case 7: *out = w7; return 1;
-    case 9: *out = w9; return 1;
-    default: return 0;
-    }
-}
-
 }  // namespace sc5

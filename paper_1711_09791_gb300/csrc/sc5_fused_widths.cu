@@ -1,0 +1,22 @@
+// sc5_fused_widths.cu -- instantiations of the fused separable kernel for
+// the odd widths other than 5 (3, 7, 9), FP32 storage.
+#include "sc5_fused_impl.cuh"
+
+namespace sc5 {
+
+// Other odd widths (3, 7, 9) of the separable kernel: one shape each.
+int fused_width_entries_f32(int out_dtype, int taps, const FusedEntry **out)
+{
+    static const FusedEntry w3[] = {make_entry<float, float, 64, 128, 4, 3, false, 3>()};
+    static const FusedEntry w7[] = {make_entry<float, float, 128, 128, 8, 2, false, 7>()};
+    static const FusedEntry w9[] = {make_entry<float, float, 128, 128, 8, 2, false, 9>()};
+    if (out_dtype != SC5_F32) return 0;
+    switch (taps) {
+    case 3: *out = w3; return 1;
+    case 7: *out = w7; return 1;
+    case 9: *out = w9; return 1;
+    default: return 0;
+    }
+}
+
+}  // namespace sc5
