@@ -536,6 +536,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         del X, Y
         extras["layout_3RxC"] = {"ms_per_step": round(msl, 5), "frac_of_measured_hbm": round(alg / (msl / 1e3) / 1e9 / peak, 4),
                                  "vs_stacked": round(msl / ms, 3)}
+        # pixel-interleaved (HWC) images: the same pixels as RGB triples
+        X = A_dev.permute(1, 2, 0).contiguous()
+        Y = torch.empty((H - 4, W - 4, P), dtype=torch.float32, device=dev)
+        pl = sepconv5.Plan(P, H, W, P * W, P * (W - 4), layout="hwc")
+        msh, _ = timed(lambda: pl.run(X, Y, k, stream=stream), k2, 3)
+        pl.close()
+        del X, Y
+        extras["layout_HWC"] = {"ms_per_step": round(msh, 5), "frac_of_measured_hbm": round(alg / (msh / 1e3) / 1e9 / peak, 4),
+                                "vs_planar": round(msh / ms, 3)}
         # other odd kernel widths through the fused kernel
         widths = {}
         for n in (3, 7, 9):

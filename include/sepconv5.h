@@ -97,6 +97,16 @@ typedef enum {
                                FP32, sepconv5_run_K takes any K */
 } sc5_algo;
 
+/* Image layouts.  SC5_LAYOUT_HWC: pixel-interleaved 3-plane images (RGB),
+ * value (p, y, x) at y*pitch + 3*x + p for input and output alike (the VALID
+ * output row holds 3*(W-4) values); pitches count values.  Built for planes
+ * = 3, SC5_ALGO_FUSED, width 5, SC5_BORDER_VALID and every storage pair;
+ * in_pitch * element size must be a multiple of 16 bytes. */
+typedef enum {
+    SC5_LAYOUT_PLANAR = 0,
+    SC5_LAYOUT_HWC = 1
+} sc5_layout;
+
 /* Plan descriptor.  Pitches and plane strides are in elements of the
  * respective dtype.
  * taps: the kernel width n.  The paper uses 5 (Sec. 4); 3, 7 and 9 are built
@@ -127,6 +137,7 @@ typedef struct {
     int32_t ctas_per_sm;           /* 0 = as many as fit */
     int64_t in_plane_stride, out_plane_stride;
     int32_t taps;                  /* kernel width: 0 or 5 (the paper's), or 3, 7, 9 */
+    int32_t layout;                /* sc5_layout */
 } sc5_plan_desc;
 
 typedef struct sc5_plan_s *sc5_plan;

@@ -290,6 +290,62 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
 }
 }  // namespace sc5
 
+// Pixel-interleaved 3-plane images: validation and plan.
+static sc5_status plan_hwc(const sc5_plan_desc &d, sc5_plan *out)
+{
+    if (d.planes != 3) return fail(SC5_EINVAL, "the HWC layout is built for 3 planes");
+    if (d.algo != SC5_ALGO_FUSED || d.taps != kTaps || d.border != SC5_BORDER_VALID)
+        return fail(SC5_EINVAL, "the HWC layout is built for the fused form, width 5, VALID border");
+    if (d.in_plane_stride || d.out_plane_stride) return fail(SC5_EINVAL, "plane strides do not apply to HWC");
+    if (d.H < 5 || d.W < 5 || d.H > 65535 * 8 || d.W > (1 << 28)) return fail(SC5_EINVAL, "bad image size");
+    const int ei = dtype_bytes(d.in_dtype), th = hwc_tile_h(d.in_dtype, d.out_dtype);
+    if (!ei || !th) return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built", d.in_dtype, d.out_dtype);
+    if (d.in_pitch < 3ll * d.W || (d.in_pitch * ei) % 16)
+        return fail(SC5_EINVAL, "HWC in_pitch must be >= 3*W values with in_pitch * element size a multiple of 16");
+    if (d.out_pitch < 3ll * (d.W - kHalo)) return fail(SC5_EINVAL, "HWC out_pitch must be >= 3*(W-4) values");
+    sc5_plan p = new (std::nothrow) sc5_plan_s;
+    if (!p) return fail(SC5_ENOMEM, "host allocation failed");
+    p->d = d;
+    cudaGetDevice(&p->device);
+    p->shape = FusedShape{th, 128, 4, 0};
+    if (cudaEventCreateWithFlags(&p->ws_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete p;
+        return fail(SC5_ECUDA, "cudaEventCreate failed");
+    }
+    *out = p;
+    return SC5_OK;
+}
+
+static sc5_status run_hwc(sc5_plan p, const void *in, void *out, const float *k, float in_scale, float out_scale,
+                          cudaStream_t s)
+{
+    const sc5_plan_desc &d = p->d;
+    const int ei = dtype_bytes(d.in_dtype), eo = dtype_bytes(d.out_dtype);
+    if (!in || !out) return fail(SC5_EINVAL, "null image pointer");
+    if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % eo) return fail(SC5_EINVAL, "output not aligned to its element size");
+    if (!(in_scale > 0.f) || !std::isfinite(in_scale) || !(out_scale > 0.f) || !std::isfinite(out_scale))
+        return fail(SC5_EINVAL, "scales must be finite and > 0");
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    const int Hv = d.H - kHalo, Wv = d.W - kHalo;
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    const char *a_end = a + (static_cast<size_t>(d.H - 1) * d.in_pitch + 3ull * d.W) * ei;
+    const char *b_end = b + (static_cast<size_t>(Hv - 1) * d.out_pitch + 3ull * Wv) * eo;
+    if (a < b_end && b < a_end) return fail(SC5_EINVAL, "input and output overlap");
+    CUtensorMap m;
+    sc5_status st = encode_image_map(&m, d.in_dtype, in, 1, d.H, 3 * d.W, d.in_pitch, hwc_box_cols(d.in_dtype),
+                                     p->shape.tile_h + kHalo);
+    if (st != SC5_OK) return st;
+    alignas(64) unsigned char desc[512];
+    if (hwc_desc_size() > sizeof desc) return fail(SC5_ECUDA, "descriptor too large");
+    const bool vec = reinterpret_cast<uintptr_t>(out) % (4 * eo) == 0 && d.out_pitch % 4 == 0;
+    const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
+    hwc_fill(desc, m, out, d.out_pitch, Hv, Wv, p->shape.tile_h, k, oscale, vec);
+    const int64_t ntiles = static_cast<int64_t>((Wv + 127) / 128) * ((Hv + p->shape.tile_h - 1) / p->shape.tile_h);
+    cudaError_t e = launch_hwc(d.in_dtype, d.out_dtype, desc, ntiles, s);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "HWC launch");
+}
+
 extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
 {
     clear_error();
@@ -297,6 +353,8 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     *out = nullptr;
     sc5_plan_desc d = *desc;
     if (d.taps == 0) d.taps = kTaps;
+    if (d.layout == SC5_LAYOUT_HWC) return plan_hwc(d, out);
+    if (d.layout != SC5_LAYOUT_PLANAR) return fail(SC5_EINVAL, "unknown layout %d", d.layout);
     if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS && d.algo != SC5_ALGO_DIRECT)
         return fail(SC5_EINVAL, "unknown algo %d", d.algo);
     if (d.taps != 3 && d.taps != 5 && d.taps != 7 && d.taps != 9)
@@ -415,6 +473,7 @@ extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const 
     clear_error();
     if (!p || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (d.layout == SC5_LAYOUT_HWC) return run_hwc(p, in, out, k, in_scale, out_scale, static_cast<cudaStream_t>(stream));
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride,
                                 taps_of(d));
@@ -437,7 +496,8 @@ extern "C" sc5_status sepconv5_run_K(sc5_plan p, const void *in, void *out, cons
     clear_error();
     if (!p || !K) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
-    if (d.algo != SC5_ALGO_DIRECT) return fail(SC5_EINVAL, "sepconv5_run_K needs a plan with algo SC5_ALGO_DIRECT");
+    if (d.algo != SC5_ALGO_DIRECT || d.layout != SC5_LAYOUT_PLANAR)
+        return fail(SC5_EINVAL, "sepconv5_run_K needs a planar plan with algo SC5_ALGO_DIRECT");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride);
     if (st != SC5_OK) return st;
@@ -458,7 +518,8 @@ extern "C" sc5_status sepconv5_run_inplace(sc5_plan p, void *img, const float k[
     if (d.in_dtype != d.out_dtype || d.border != SC5_BORDER_KEEP || d.out_pitch != d.in_pitch)
         return fail(SC5_EINVAL, "in-place needs in_dtype == out_dtype, border KEEP and out_pitch == in_pitch");
     if (!default_strides(d)) return fail(SC5_EINVAL, "in-place takes stacked planes (plane strides 0)");
-    if (taps_of(d) != kTaps) return fail(SC5_EINVAL, "in-place is built for width 5");
+    if (taps_of(d) != kTaps || d.layout != SC5_LAYOUT_PLANAR)
+        return fail(SC5_EINVAL, "in-place is built for planar images of width 5");
     if (reinterpret_cast<uintptr_t>(img) % 16) return fail(SC5_EINVAL, "image must be 16-byte aligned");
     if (!(scale > 0.f) || !std::isfinite(scale)) return fail(SC5_EINVAL, "scale must be finite and > 0");
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
@@ -500,7 +561,8 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
     if (!p || !host_in || !host_out || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
     if (!default_strides(d)) return fail(SC5_EINVAL, "the offload call takes stacked planes (plane strides 0)");
-    if (taps_of(d) != kTaps) return fail(SC5_EINVAL, "the offload call is built for width 5");
+    if (taps_of(d) != kTaps || d.layout != SC5_LAYOUT_PLANAR)
+        return fail(SC5_EINVAL, "the offload call is built for planar images of width 5");
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, false);
     if (st != SC5_OK) return st;
@@ -592,6 +654,8 @@ extern "C" sc5_status sepconv5_hpass(sc5_plan p, const void *in, float *T, int64
     clear_error();
     if (!p || !in || !T || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (d.layout != SC5_LAYOUT_PLANAR || taps_of(d) != kTaps)
+        return fail(SC5_EINVAL, "the separate passes take planar images of width 5");
     if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
         return fail(SC5_EINVAL, "T needs t_pitch >= W-4, a multiple of 4, and 16-byte alignment");
     if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
@@ -608,6 +672,8 @@ extern "C" sc5_status sepconv5_vpass(sc5_plan p, const float *T, int64_t t_pitch
     clear_error();
     if (!p || !out || !T || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (d.layout != SC5_LAYOUT_PLANAR || taps_of(d) != kTaps)
+        return fail(SC5_EINVAL, "the separate passes take planar images of width 5");
     if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
         return fail(SC5_EINVAL, "T needs t_pitch >= W-4, a multiple of 4, and 16-byte alignment");
     if (!(in_scale > 0.f) || !(out_scale > 0.f) || !std::isfinite(in_scale) || !std::isfinite(out_scale))
@@ -709,7 +775,8 @@ extern "C" sc5_status sepconv5_run_batch(sc5_plan p, int32_t n, const sc5_image 
     clear_error();
     if (!p) return fail(SC5_EINVAL, "null plan");
     if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
-    if (taps_of(p->d) != kTaps) return fail(SC5_EINVAL, "batches are built for width 5");
+    if (taps_of(p->d) != kTaps || p->d.layout != SC5_LAYOUT_PLANAR)
+        return fail(SC5_EINVAL, "batches are built for planar images of width 5");
     int idx = 0, ctas = 1;
     sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
     if (st != SC5_OK) return st;
@@ -783,7 +850,8 @@ extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_ima
     if (!p || !out) return fail(SC5_EINVAL, "null argument");
     *out = nullptr;
     if (p->d.algo != SC5_ALGO_FUSED) return fail(SC5_EINVAL, "batches run the fused form only");
-    if (taps_of(p->d) != kTaps) return fail(SC5_EINVAL, "batches are built for width 5");
+    if (taps_of(p->d) != kTaps || p->d.layout != SC5_LAYOUT_PLANAR)
+        return fail(SC5_EINVAL, "batches are built for planar images of width 5");
     int idx = 0, ctas = 1;
     sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
     if (st != SC5_OK) return st;

@@ -102,6 +102,8 @@ static int *status_ptr()
     return ptrs[dev];
 }
 
+int *status_word() { return status_ptr(); }
+
 int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct, int taps)
 {
     const FusedEntry *e;

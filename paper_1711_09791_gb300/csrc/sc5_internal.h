@@ -69,6 +69,15 @@ cudaError_t launch_fused_batch(int in_dtype, int out_dtype, int idx, const ImgDe
                                const TileRec *tiles, int64_t ntiles, int grid, cudaStream_t st);
 cudaError_t read_and_clear_device_status(cudaStream_t st, int32_t *code);
 cudaError_t launch_wait_selftest(int limit_us, cudaStream_t st);
+int *status_word();  // device address of the status word on the current device
+
+// Pixel-interleaved (HWC, 3 planes) fused kernel (sc5_hwc.cu).
+int hwc_box_cols(int in_dtype);              // values per TMA box row
+int hwc_tile_h(int in_dtype, int out_dtype); // output rows per tile (0: pair not built)
+size_t hwc_desc_size();
+void hwc_fill(void *desc, const CUtensorMap &m, void *out, int64_t out_pitch, int Hv, int Wv, int tile_h,
+              const float *k, float oscale, bool vec);
+cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc, int64_t ntiles, cudaStream_t st);
 
 // Two-pass kernels and helpers (sc5_twopass.cu).
 cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,

@@ -22,6 +22,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EAGAIN", "ETIMEDOUT", "ENOTF
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8e4m3": 3}
 DTYPE_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "fp8e4m3": 1}
 BORDERS = {"valid": 0, "keep": 1}
+LAYOUTS = {"planar": 0, "hwc": 1}
 ALGOS = {"fused": 0, "two_pass": 1, "direct": 2}
 
 
@@ -37,7 +38,8 @@ class PlanDesc(ctypes.Structure):
                 ("in_pitch", c_int64), ("out_pitch", c_int64),
                 ("in_dtype", c_int32), ("out_dtype", c_int32), ("border", c_int32), ("algo", c_int32),
                 ("tile_h", c_int32), ("tile_w", c_int32), ("stages", c_int32), ("ctas_per_sm", c_int32),
-                ("in_plane_stride", c_int64), ("out_plane_stride", c_int64), ("taps", c_int32)]
+                ("in_plane_stride", c_int64), ("out_plane_stride", c_int64), ("taps", c_int32),
+                ("layout", c_int32)]
 
 
 class Image(ctypes.Structure):
@@ -154,7 +156,7 @@ class Plan:
 
     def __init__(self, planes: int, H: int, W: int, in_pitch: int | None = None, out_pitch: int | None = None,
                  in_dtype="f32", out_dtype=None, border="valid", algo="fused", tile_h=0, tile_w=0, stages=0,
-                 ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0, taps=5):
+                 ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0, taps=5, layout="planar"):
         out_dtype = in_dtype if out_dtype is None else out_dtype
         b = BORDERS[border] if isinstance(border, str) else int(border)
         d = PlanDesc()
@@ -167,6 +169,7 @@ class Plan:
         d.tile_h, d.tile_w, d.stages, d.ctas_per_sm = tile_h, tile_w, stages, ctas_per_sm
         d.in_plane_stride, d.out_plane_stride = in_plane_stride, out_plane_stride
         d.taps = taps
+        d.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
         self.taps = taps
         halo = taps - 1
         if out_pitch is None:
