@@ -2,7 +2,8 @@
 // paper's tuning of the thread / task count, Sec. 4 and Sec. 7: 100 threads
 // was the chosen "magic number", 120 helped some images).  For each size
 // class of plane area and each dtype pair it times every compiled tile shape
-// at every feasible CTAs-per-SM count on a synthetic image and keeps the
+// at every feasible CTAs-per-SM count on a batch of synthetic images of that
+// class (at least 512 MB of input, replayed from a CUDA graph) and keeps the
 // fastest.  The table lives in the process and can be saved / loaded as JSON
 // (one entry per line) keyed by GPU name.
 #include <algorithm>
@@ -71,9 +72,10 @@ static std::string gpu_name()
     return prop.name;
 }
 
-// Median time in microseconds of `reps` runs of one configuration.
-static sc5_status time_config(int in, int out, int H, int W, int idx, int ctas, void *din, void *dout,
-                              int reps, double *us)
+// Median time in microseconds of `reps` replays of one configuration on a
+// batch of n images of one size (a graph-captured batch launch).
+static sc5_status time_config(int in, int out, int H, int W, int n, int idx, int ctas, unsigned char *din,
+                              unsigned char *dout, size_t in_img, size_t out_img, int reps, double *us)
 {
     FusedShape sh;
     fused_shape(in, out, idx, &sh);
@@ -82,7 +84,7 @@ static sc5_status time_config(int in, int out, int H, int W, int idx, int ctas, 
     d.H = H;
     d.W = W;
     const int ei = dtype_bytes(in);
-    d.in_pitch = (W * ei + 15) / 16 * 16 / ei;
+    d.in_pitch = (static_cast<int64_t>(W) * ei + 15) / 16 * 16 / ei;
     d.out_pitch = (W - 4 + 3) / 4 * 4;
     d.in_dtype = in;
     d.out_dtype = out;
@@ -95,22 +97,44 @@ static sc5_status time_config(int in, int out, int H, int W, int idx, int ctas, 
     sc5_plan p = nullptr;
     sc5_status st = sepconv5_plan(&d, &p);
     if (st != SC5_OK) return st;
-    const float k[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
-    cudaEvent_t a, b;
+    std::vector<sc5_image> imgs(n);
+    for (int i = 0; i < n; ++i) {
+        sc5_image &im = imgs[i];
+        im.in = din + i * in_img;
+        im.out = dout + i * out_img;
+        im.H = H;
+        im.W = W;
+        im.in_pitch = d.in_pitch;
+        im.out_pitch = d.out_pitch;
+        const float k[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+        for (int t = 0; t < 5; ++t) im.k[t] = k[t];
+        im.in_scale = im.out_scale = 1.f;
+    }
+    sc5_batch b = nullptr;
+    st = sepconv5_batch_create(p, n, imgs.data(), &b);
+    if (st != SC5_OK) {
+        sepconv5_plan_destroy(p);
+        return st;
+    }
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEvent_t a, e;
     cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    cudaEventCreate(&e);
     std::vector<float> ts;
     for (int r = 0; r < reps + 2 && st == SC5_OK; ++r) {
-        cudaEventRecord(a, 0);
-        st = sepconv5_run(p, din, dout, k, 1.f, 1.f, nullptr);
-        cudaEventRecord(b, 0);
-        cudaEventSynchronize(b);
+        cudaEventRecord(a, s);
+        st = sepconv5_batch_launch(b, s);
+        cudaEventRecord(e, s);
+        cudaEventSynchronize(e);
         float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
+        cudaEventElapsedTime(&ms, a, e);
         if (r >= 2) ts.push_back(ms);
     }
     cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    cudaEventDestroy(e);
+    cudaStreamDestroy(s);
+    sepconv5_batch_destroy(b);
     sepconv5_plan_destroy(p);
     if (st != SC5_OK) return st;
     std::sort(ts.begin(), ts.end());
@@ -151,7 +175,11 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
         return SC5_OK;
     }
     if (!dtypes || n_pairs < 1) return fail(SC5_EINVAL, "no dtype pairs given");
-    const int reps = mode >= 2 ? 20 : 5;
+    const int reps = mode >= 2 ? 10 : 3;
+    // Each class is tuned on a batch of images of its representative size
+    // that together hold at least kTuneBytes of input: far more than the L2,
+    // so the timings see the HBM-streaming behaviour of real batches.
+    constexpr size_t kTuneBytes = 512ull << 20;
     std::vector<TuneEntry> found;
     for (int q = 0; q < n_pairs; ++q) {
         const int in = dtypes[2 * q], out = dtypes[2 * q + 1];
@@ -161,12 +189,15 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
             int H, W;
             class_shape(c, &H, &W);
             const int ei = dtype_bytes(in), eo = dtype_bytes(out);
-            const size_t in_pitch = (W * ei + 15) / 16 * 16 / ei;
+            const size_t in_pitch = (static_cast<size_t>(W) * ei + 15) / 16 * 16 / ei;
             const size_t out_pitch = (W - 4 + 3) / 4 * 4;
-            void *din = nullptr, *dout = nullptr;
-            cudaError_t e = cudaMalloc(&din, 3 * H * in_pitch * ei);
-            if (e == cudaSuccess) e = cudaMalloc(&dout, 3 * (H - 4) * out_pitch * eo);
-            if (e == cudaSuccess) e = cudaMemset(din, 0x3c, 3 * H * in_pitch * ei);
+            const size_t in_img = (3 * H * in_pitch * ei + 255) / 256 * 256;
+            const size_t out_img = (3 * (H - 4) * out_pitch * eo + 255) / 256 * 256;
+            const int n = static_cast<int>(std::max<size_t>(1, (kTuneBytes + in_img - 1) / in_img));
+            unsigned char *din = nullptr, *dout = nullptr;
+            cudaError_t e = cudaMalloc(&din, n * in_img);
+            if (e == cudaSuccess) e = cudaMalloc(&dout, n * out_img);
+            if (e == cudaSuccess) e = cudaMemset(din, 0x3c, n * in_img);
             if (e != cudaSuccess) {
                 cudaFree(din);
                 cudaFree(dout);
@@ -177,7 +208,7 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
                 const int maxc = fused_max_ctas_per_sm(in, out, idx);
                 for (int ctas = 1; ctas <= maxc; ++ctas) {
                     double us = 0;
-                    sc5_status st = time_config(in, out, H, W, idx, ctas, din, dout, reps, &us);
+                    sc5_status st = time_config(in, out, H, W, n, idx, ctas, din, dout, in_img, out_img, reps, &us);
                     if (st != SC5_OK) {
                         cudaFree(din);
                         cudaFree(dout);
