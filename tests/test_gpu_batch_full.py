@@ -2,7 +2,8 @@
 about 241 Mpix x 3 planes), in the launch configuration the benchmark times:
 autotuned shape, one persistent launch replayed from a CUDA graph.  Sampled
 pixels of every image are checked against the FP64 oracle one by one (a 5x5
-window per pixel), in FP32 and in bfloat16 storage."""
+window per pixel), in FP32 and in every stored format (fp8 with its per-image
+scale 448/max)."""
 import numpy as np
 import pytest
 
@@ -13,24 +14,27 @@ from tests import _util as U
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "fp8e4m3"])
 def test_full_batch_sampled(dtype):
     import torch
     from paper_1711_09791_gb300 import sepconv5 as sc5
     sc5.load()
     shapes = synth.batch_shapes(3, 256)
     sc5.autotune(1, [(dtype, dtype)])
-    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16,
+           "fp8e4m3": torch.float8_e4m3fn}[dtype]
     es = sc5.DTYPE_BYTES[dtype]
     imgs = []
     for i, (h, w) in enumerate(shapes):
         x = torch.from_numpy(synth.image(3000 + i, h, w)).cuda()
+        s = 448.0 / float(x.abs().max()) if dtype == "fp8e4m3" else 1.0
         pitch = -(-w * es // 16) * 16 // es
         A = torch.zeros((3, h, pitch), dtype=tdt, device="cuda")
-        A[:, :, :w] = x.to(tdt)
-        out = torch.full((3, h - 4, w - 4), float("nan"), dtype=tdt, device="cuda")
-        imgs.append({"in": A, "out": out, "H": h, "W": w, "in_pitch": pitch, "out_pitch": w - 4,
-                     "k": synth.kernel_normalised(3000 + i)})
+        A[:, :, :w] = (x * s).to(tdt)
+        op = -(-(w - 4) // 4) * 4
+        out = torch.zeros((3, h - 4, op), dtype=tdt, device="cuda")
+        imgs.append({"in": A, "out": out, "H": h, "W": w, "in_pitch": pitch, "out_pitch": op,
+                     "k": synth.kernel_normalised(3000 + i), "in_scale": s, "out_scale": s})
     plan = sc5.Plan(3, 64, 64, in_dtype=dtype)
     b = sc5.Batch(plan, imgs)
     b.launch()
@@ -45,13 +49,14 @@ def test_full_batch_sampled(dtype):
         p[:4] = 0
         y[:4] = torch.tensor([0, 0, h - 5, h - 5], device="cuda")
         x[:4] = torch.tensor([0, w - 5, 0, w - 5], device="cuda")
-        win = im["in"].float()[p[:, None, None], (y[:, None] + idx)[:, :, None], (x[:, None] + idx)[:, None, :]]
+        s = im["in_scale"]
+        win = im["in"].float()[p[:, None, None], (y[:, None] + idx)[:, :, None], (x[:, None] + idx)[:, None, :]] / s
         ref = oracle.direct(win.double().cpu().numpy(), np.asarray(im["k"], np.float64))[:, 0, 0]
-        got = im["out"][p, y, x].float().double().cpu().numpy()
+        got = (im["out"][p, y, x].float() / s).double().cpu().numpy()
         if dtype == "f32":
             assert U.max_abs(got, ref) <= U.FP32_TOL
         else:
-            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, "bf16", 1.0, U.FP32_TOL))
-        assert not torch.isnan(im["out"].float()).any()
+            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, s, U.FP32_TOL))
+        assert not torch.isnan(im["out"][:, :, :w - 4].float()).any()
     b.close()
     plan.close()
