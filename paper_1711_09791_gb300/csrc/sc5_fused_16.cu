@@ -6,14 +6,14 @@ namespace sc5 {
 
 #define SC5_SHAPES_16(TI, TO)                                   \
     {                                                           \
-        make_entry<TI, TO, 64, 128, 4, 6>(),                    \
+        make_entry<TI, TO, 128, 128, 16, 2>(), /* default */    \
+        make_entry<TI, TO, 128, 128, 16, 3>(),                  \
         make_entry<TI, TO, 128, 128, 8, 4>(),                   \
+        make_entry<TI, TO, 64, 128, 4, 6>(),                    \
         make_entry<TI, TO, 64, 128, 4, 4>(),                    \
         make_entry<TI, TO, 32, 128, 2, 8>(),                    \
         make_entry<TI, TO, 120, 128, 4, 4>(),                   \
         make_entry<TI, TO, 240, 128, 8, 3>(),                   \
-        make_entry<TI, TO, 128, 128, 16, 3>(),                  \
-        make_entry<TI, TO, 128, 128, 16, 2>(),                  \
     }
 
 int fused_entries_16(int in_dtype, int out_dtype, const FusedEntry **out)

@@ -6,6 +6,8 @@ namespace sc5 {
 
 #define SC5_SHAPES_8(TI, TO)                                    \
     {                                                           \
+        make_entry<TI, TO, 128, 128, 16, 3>(), /* default */    \
+        make_entry<TI, TO, 128, 128, 16, 5>(),                  \
         make_entry<TI, TO, 128, 128, 8, 6>(),                   \
         make_entry<TI, TO, 64, 128, 4, 8>(),                    \
         make_entry<TI, TO, 128, 128, 8, 4>(),                   \
@@ -13,8 +15,6 @@ namespace sc5 {
         make_entry<TI, TO, 32, 128, 2, 12>(),                   \
         make_entry<TI, TO, 240, 128, 8, 4>(),                   \
         make_entry<TI, TO, 120, 128, 4, 6>(),                   \
-        make_entry<TI, TO, 128, 128, 16, 5>(),                  \
-        make_entry<TI, TO, 128, 128, 16, 3>(),                  \
     }
 
 int fused_entries_fp8(int out_dtype, const FusedEntry **out)

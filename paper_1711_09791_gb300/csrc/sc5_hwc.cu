@@ -268,14 +268,14 @@ static HwcEntry hwc_entry()
 
 static bool hwc_lookup(int in_dtype, int out_dtype, HwcEntry *e)
 {
-    // (tile rows, rows per lane, stages): 8 consumer warps, 3 planes per lane
-    static const HwcEntry f32_f32 = hwc_entry<float, float, 32, 4, 3>();
-    static const HwcEntry bf_bf = hwc_entry<bf16_t, bf16_t, 32, 4, 4>();
-    static const HwcEntry bf_f32 = hwc_entry<bf16_t, float, 32, 4, 4>();
-    static const HwcEntry h_h = hwc_entry<f16_t, f16_t, 32, 4, 4>();
-    static const HwcEntry h_f32 = hwc_entry<f16_t, float, 32, 4, 4>();
-    static const HwcEntry e_e = hwc_entry<fp8e4m3_t, fp8e4m3_t, 32, 4, 6>();
-    static const HwcEntry e_f32 = hwc_entry<fp8e4m3_t, float, 32, 4, 6>();
+    // (tile rows, rows per lane, stages): 16 consumer warps, 3 planes per lane
+    static const HwcEntry f32_f32 = hwc_entry<float, float, 64, 4, 2>();
+    static const HwcEntry bf_bf = hwc_entry<bf16_t, bf16_t, 64, 4, 3>();
+    static const HwcEntry bf_f32 = hwc_entry<bf16_t, float, 64, 4, 3>();
+    static const HwcEntry h_h = hwc_entry<f16_t, f16_t, 64, 4, 3>();
+    static const HwcEntry h_f32 = hwc_entry<f16_t, float, 64, 4, 3>();
+    static const HwcEntry e_e = hwc_entry<fp8e4m3_t, fp8e4m3_t, 64, 4, 5>();
+    static const HwcEntry e_f32 = hwc_entry<fp8e4m3_t, float, 64, 4, 5>();
     const HwcEntry *r = nullptr;
     if (in_dtype == SC5_F32 && out_dtype == SC5_F32) r = &f32_f32;
     if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) r = &bf_bf;

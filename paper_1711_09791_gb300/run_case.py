@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--H", type=int, default=8192)
     ap.add_argument("--W", type=int, default=8192)
     ap.add_argument("--tile", default="", help="TH,TW,stages override")
+    ap.add_argument("--layout", default="planar", choices=["planar", "hwc"])
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -42,14 +43,23 @@ def main():
     x = torch.rand((P, H, W), generator=g, device="cuda") * 255.0
     scale = 448.0 / float(x.max()) if a.dtype == "fp8e4m3" else 1.0
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}
-    A = torch.zeros((P, H, pitch), dtype=tdt[a.dtype], device="cuda")
-    A[:, :, :W] = (x * scale).to(tdt[a.dtype])
-    del x
-    out = torch.empty((P, H - 4, opitch), dtype=tdt[out_dtype], device="cuda")
     th = tw = st = 0
     if a.tile:
         th, tw, st = (int(v) for v in a.tile.split(","))
-    plan = sc5.Plan(P, H, W, pitch, opitch, a.dtype, out_dtype, "valid", a.algo, th, tw, st, a.ctas)
+    if a.layout == "hwc":
+        # the same pixels as RGB triples: value (p, y, x) at y * pitch + 3x + p
+        pitch = -(-3 * W * es // 16) * 16 // es
+        opitch = -(-3 * (W - 4) // 4) * 4
+        A = torch.zeros((H, pitch), dtype=tdt[a.dtype], device="cuda")
+        A[:, :3 * W] = (x * scale).permute(1, 2, 0).reshape(H, 3 * W).to(tdt[a.dtype])
+        out = torch.empty((H - 4, opitch), dtype=tdt[out_dtype], device="cuda")
+    else:
+        A = torch.zeros((P, H, pitch), dtype=tdt[a.dtype], device="cuda")
+        A[:, :, :W] = (x * scale).to(tdt[a.dtype])
+        out = torch.empty((P, H - 4, opitch), dtype=tdt[out_dtype], device="cuda")
+    del x
+    plan = sc5.Plan(P, H, W, pitch, opitch, a.dtype, out_dtype, "valid", a.algo, th, tw, st, a.ctas,
+                    layout=a.layout)
     k = synth.kernel_normalised(2)
     out_scale = scale if out_dtype == "fp8e4m3" else 1.0
     stream = torch.cuda.current_stream()
@@ -70,7 +80,7 @@ def main():
         raise SystemExit("a kernel reported a device error")
     plan.close()
     print(json.dumps({"dtype": a.dtype, "out": out_dtype, "algo": a.algo, "planes": P, "H": H, "W": W,
-                      "tile": a.tile or "default", "ms": round(ms, 5), "gbs": round(alg / ms / 1e6, 1),
+                      "layout": a.layout, "tile": a.tile or "default", "ms": round(ms, 5), "gbs": round(alg / ms / 1e6, 1),
                       "mpix_s": round(H * W / ms / 1e3, 1)}))
 
 
