@@ -346,7 +346,11 @@ def leg_batch(sc5, synth, oracle, stream, dtypes):
         alg = sum(P * h * w * sc5.DTYPE_BYTES[dtype] + P * (h - 4) * (w - 4) * sc5.DTYPE_BYTES[out_dtype]
                   for h, w in shapes)
         ea, er = _sample_errors(oracle, imgs, outs, dtype, out_dtype)
+        # narrow-to-narrow formats move 2-4 bytes per pixel: the SMs' instruction issue and FMA
+        # pipe bound them before HBM does (profiles/fused_bf16_3x8192x8192.md)
+        bound = "sm_issue" if out_dtype != "f32" and dtype != "f32" else "hbm"
         results[f"{dtype}->{out_dtype}"] = {
+            "bound": bound,
             "ms": round(ms, 4), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "achieved_gbs": round(alg / ms / 1e6, 1),
             "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4), "tiles": info["tiles"], "ctas": info["ctas"],
             "tile": f"{info['tile_h']}x{info['tile_w']}", "max_abs_err_vs_fp64": ea, "max_rel_err_vs_fp64": er,

@@ -1,0 +1,100 @@
+/*
+ * A plain C user of libsepconv5: only <sepconv5.h> and the CUDA runtime.
+ *   abi_example host   -- host-only calls (no GPU needed): the compiled
+ *                         shapes, a refused descriptor, the error message.
+ *   abi_example gpu    -- convolve a 3 x 67 x 133 image with k = e_2 (the
+ *                         identity tap) and check the result equals the
+ *                         interior of the input exactly.
+ * Prints "OK" and exits 0 on success.
+ */
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "sepconv5.h"
+
+static int host_checks(void)
+{
+    int32_t cfg[3 * 32], n = 0;
+    if (sepconv5_fused_configs(SC5_F32, SC5_F32, cfg, 32, &n) != SC5_OK || n < 1) {
+        fprintf(stderr, "fused_configs failed: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    if (cfg[1] != 128) return 1;
+    sc5_plan_desc d;
+    memset(&d, 0, sizeof d);
+    d.planes = 3;
+    d.H = 4; /* too small */
+    d.W = 64;
+    d.in_pitch = 64;
+    d.out_pitch = 60;
+    sc5_plan p = NULL;
+    if (sepconv5_plan(&d, &p) != SC5_EINVAL || p != NULL) return 1;
+    if (strlen(sepconv5_last_error()) == 0) return 1;
+    return 0;
+}
+
+static int gpu_checks(void)
+{
+    const int P = 3, H = 67, W = 133, pitch = 136, Hv = H - 4, Wv = W - 4;
+    const size_t n_in = (size_t)P * H * pitch, n_out = (size_t)P * Hv * Wv;
+    float *a = (float *)malloc(n_in * sizeof(float)), *b = (float *)malloc(n_out * sizeof(float));
+    for (size_t i = 0; i < n_in; ++i) a[i] = (float)((i * 2654435761u) % 256u);
+    float *da = NULL, *db = NULL;
+    if (cudaMalloc((void **)&da, n_in * sizeof(float)) != cudaSuccess) return 1;
+    if (cudaMalloc((void **)&db, n_out * sizeof(float)) != cudaSuccess) return 1;
+    cudaMemcpy(da, a, n_in * sizeof(float), cudaMemcpyHostToDevice);
+    sc5_plan_desc d;
+    memset(&d, 0, sizeof d);
+    d.planes = P;
+    d.H = H;
+    d.W = W;
+    d.in_pitch = pitch;
+    d.out_pitch = Wv;
+    d.in_dtype = d.out_dtype = SC5_F32;
+    d.border = SC5_BORDER_VALID;
+    d.algo = SC5_ALGO_FUSED;
+    sc5_plan p = NULL;
+    if (sepconv5_plan(&d, &p) != SC5_OK) {
+        fprintf(stderr, "plan: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    const float k[5] = {0.f, 0.f, 1.f, 0.f, 0.f};
+    if (sepconv5_run(p, da, db, k, 1.f, 1.f, NULL) != SC5_OK) {
+        fprintf(stderr, "run: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    int32_t code = 0;
+    if (sepconv5_device_status(NULL, &code) != SC5_OK) return 1;
+    cudaMemcpy(b, db, n_out * sizeof(float), cudaMemcpyDeviceToHost);
+    for (int pl = 0; pl < P; ++pl)
+        for (int y = 0; y < Hv; ++y)
+            for (int x = 0; x < Wv; ++x)
+                if (b[((size_t)pl * Hv + y) * Wv + x] != a[((size_t)pl * H + y + 2) * pitch + x + 2]) {
+                    fprintf(stderr, "mismatch at %d %d %d\n", pl, y, x);
+                    return 1;
+                }
+    sepconv5_plan_destroy(p);
+    cudaFree(da);
+    cudaFree(db);
+    free(a);
+    free(b);
+    return 0;
+}
+
+int main(int argc, char **argv)
+{
+    const int gpu = argc > 1 && strcmp(argv[1], "gpu") == 0;
+    if (host_checks()) {
+        fprintf(stderr, "host checks failed\n");
+        return 1;
+    }
+    if (gpu && gpu_checks()) {
+        fprintf(stderr, "gpu checks failed\n");
+        return 1;
+    }
+    printf("OK\n");
+    return 0;
+}

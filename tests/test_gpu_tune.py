@@ -13,6 +13,7 @@ def test_autotune_table_roundtrip(tmp_path):
     from paper_1711_09791_gb300 import sepconv5 as sc5
     sc5.load()
     path = str(tmp_path / "tune.json")
+    sc5.autotune(0, [])  # start from an empty table (earlier tests may have tuned other pairs)
     sc5.autotune(1, [("f32", "f32"), ("bf16", "bf16")], path)
     table = json.load(open(path))
     assert table["gpu"] == torch.cuda.get_device_name(0)

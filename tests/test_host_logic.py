@@ -1,0 +1,93 @@
+"""Host-side logic that needs no GPU: the seeded generators, the stored-format
+conversions (checked against the oracle's pinned decoders), the benchmark's
+helpers, and the binding's argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_09791_gb300 import synth
+
+
+def test_generators_are_seeded_and_in_range():
+    a, b = synth.image(3, 17, 19), synth.image(3, 17, 19)
+    assert np.array_equal(a, b) and a.dtype == np.float32 and a.shape == (3, 17, 19)
+    assert a.min() >= 0.0 and a.max() < 255.0
+    assert not np.array_equal(a, synth.image(4, 17, 19))
+    p = synth.image(3, 5, 6, pitch=8)
+    assert np.all(np.isnan(p[:, :, 6:])) and np.array_equal(p[:, :, :6], synth.image(3, 5, 6))
+    k = synth.kernel_normalised(9)
+    assert k.dtype == np.float32 and abs(float(k.astype(np.float64).sum()) - 1.0) < 1e-6 and np.all(k > 0)
+    assert np.array_equal(synth.kernel_binomial() * 16, np.array([1, 4, 6, 4, 1], np.float32))
+
+
+def test_batch_shapes_log_uniform():
+    shapes = synth.batch_shapes(3, 256)
+    assert len(shapes) == 256 and shapes == synth.batch_shapes(3, 256)
+    hs = np.array([h for h, _ in shapes] + [w for _, w in shapes], np.float64)
+    assert hs.min() >= 64 and hs.max() <= 4096
+    # log-uniform on [64, 4096]: the mean of log2 is about 9, the spread covers the range
+    assert abs(np.log2(hs).mean() - 9.0) < 0.4 and np.log2(hs).min() < 6.5 and np.log2(hs).max() > 11.5
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16", "fp8e4m3"])
+def test_storage_rounding_is_nearest(dtype):
+    x = synth.image(12, 16, 64)
+    scale = synth.fp8_scale(x) if dtype == "fp8e4m3" else 1.0
+    codes = synth.to_storage(x, dtype, scale)
+    vals = oracle.decode(codes, dtype, scale)
+    # the decoded value is within half an ulp of the format from the original
+    mant = {"bf16": 7, "f16": 10, "fp8e4m3": 3}[dtype]
+    e = np.floor(np.log2(np.maximum(np.abs(x.astype(np.float64)) * scale, 2.0 ** -6)))
+    half_ulp = np.exp2(e - mant - 1) / scale
+    assert np.all(np.abs(vals - x) <= half_ulp * (1 + 1e-12))
+    if dtype == "fp8e4m3":
+        assert float(np.max(np.abs(x))) * scale == pytest.approx(448.0)
+
+
+def test_serve_stream_poisson():
+    s = synth.serve_stream(5, 4000, 1000.0)
+    t = np.array([a for a, _, _ in s])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0) and abs(gaps.mean() - 1e-3) < 1e-4
+    classes = np.bincount([c for _, c, _ in s], minlength=3)
+    assert np.all(classes > 1200)
+
+
+def test_bench_helpers():
+    import bench
+    assert bench.algorithmic_bytes(8192, 8192) == 3 * 8192 * 8192 * 4 + 3 * 8188 * 8188 * 4 == 1609826496
+    assert bench.whole_job_value(1, 8192 * 8192, 0.25) == pytest.approx(8192 * 8192 / 0.25e-3 / 1e6)
+    assert bench.reduce_max(1.5, 1) == 1.5
+    peaks = bench.measured_peaks()
+    if peaks is not None:
+        assert peaks["hbm_gbs"] > 1000
+    # the committed profile is read only when it matches the kernel sources
+    t = bench.profiled_traffic()
+    assert t is None or 1.4e9 < t < 1.8e9
+
+
+def test_clock_sampler_parsing():
+    import bench
+    cs = bench.ClockSampler("0")
+    cs.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
+    cs.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "garbage"]
+    r = cs.stop()
+    assert r["sm_max_mhz"] == 2070 and r["samples"] == 2 and r["reasons"] == ["sw_power_cap"]
+
+
+def test_binding_header_and_arguments():
+    from paper_1711_09791_gb300 import sepconv5
+    names = sepconv5.header_symbols()
+    for n in ("sepconv5_plan", "sepconv5_run", "sepconv5_run_K", "sepconv5_run_inplace", "sepconv5_run_host",
+              "sepconv5_run_batch", "serve_submit", "serve_poll", "sepconv5_autotune"):
+        assert n in names
+    assert sepconv5._taps([1, 2, 3, 4, 5])[4] == 5.0
+    with pytest.raises(ValueError):
+        sepconv5._taps([1, 2, 3])
+    assert len(sepconv5._taps([1, 2, 3], 3)) == 3
+    assert sepconv5._ptr(None) is None and sepconv5._ptr(1234) == 1234
+    assert math.isclose(sepconv5.DTYPE_BYTES["fp8e4m3"], 1)
