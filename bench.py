@@ -220,11 +220,29 @@ def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
         h2d()
         d2h()
 
-    th, td, tb = t(h2d), t(d2h), t(both)
+    s3, s4 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ai, ad = A_host.view(-1), A_dev.view(-1)
+    oh, od = out_host.view(-1), out_dev.view(-1)
+    hi, ho = ai.numel() // 2, oh.numel() // 2
+
+    def both_split():
+        # each direction as two contiguous halves on two streams at once
+        with torch.cuda.stream(s1):
+            ad[:hi].copy_(ai[:hi], non_blocking=True)
+        with torch.cuda.stream(s3):
+            ad[hi:].copy_(ai[hi:], non_blocking=True)
+        with torch.cuda.stream(s2):
+            oh[:ho].copy_(od[:ho], non_blocking=True)
+        with torch.cuda.stream(s4):
+            oh[ho:].copy_(od[ho:], non_blocking=True)
+
+    th, td, tb, ts = t(h2d), t(d2h), t(both), t(both_split)
     nb_in, nb_out = A_host.numel() * 4, out_host.numel() * 4
     return {"h2d_ms": round(th, 4), "d2h_ms": round(td, 4), "both_ms": round(tb, 4),
+            "both_2streams_ms": round(ts, 4),
             "h2d_gbs": round(nb_in / th / 1e6, 1), "d2h_gbs": round(nb_out / td / 1e6, 1),
-            "both_gbs": round((nb_in + nb_out) / tb / 1e6, 1)}
+            "both_gbs": round((nb_in + nb_out) / tb / 1e6, 1),
+            "both_2streams_gbs": round((nb_in + nb_out) / ts / 1e6, 1)}
 
 
 # ------------------------------------------------------------------ other configs
@@ -607,7 +625,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # the ceiling of the offload path: plain copies over the CPU-GPU link
     e2e["link"] = copy_probe(A_host, out_host, A_dev, out, dev)
     lb = e2e["link"]
-    e2e["frac_of_link"] = round(max(lb["h2d_ms"], lb["d2h_ms"], lb["both_ms"]) / e2e_ms, 4)
+    e2e["frac_of_link"] = round(min(lb["both_ms"], lb["both_2streams_ms"]) / e2e_ms, 4)
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = oracle_sample(A, k)
