@@ -237,12 +237,11 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
         int64_t issued = 0;
-        for (int64_t i = 0;; ++i) {
-            const int64_t t = blockIdx.x + i * static_cast<int64_t>(gridDim.x);
-            if (t >= ntiles) break;
-            const int s = static_cast<int>(i % S);
-            const uint32_t use = static_cast<uint32_t>(i / S);
-            if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1, kWaitLimitNs)) {
+        int s = 0;             // stage of this tile
+        uint32_t phase = 0;    // parity of the stage's current use
+        bool wrapped = false;  // every stage has been used once
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (wrapped && !mbar_wait_bounded(&empty[s], phase ^ 1u, kWaitLimitNs)) {
                 record_error(status, kDevErrTmaTimeout);
                 break;
             }
@@ -264,6 +263,11 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             mbar_arrive_expect_tx(&full[s], TX);
             tma_load_3d(smem + s * STAGE, m, &full[s], rec.tx * TW, rec.ty * TH, rec.plane);
             ++issued;
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
+                wrapped = true;
+            }
         }
         // Leave only once the loads this lane issued have landed (bounded).
         for (int64_t j = (issued > S ? issued - S : 0); j < issued; ++j)
@@ -299,14 +303,12 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         vec = d.vec != 0;
     };
     if (!BATCH) load_desc(single);
-    for (int64_t i = 0;; ++i) {
-        const int64_t t = blockIdx.x + i * static_cast<int64_t>(gridDim.x);
-        if (t >= ntiles) break;
-        const int s = static_cast<int>(i % S);
-        const uint32_t use = static_cast<uint32_t>(i / S);
-        if (!mbar_wait_bounded(&full[s], use & 1, kWaitLimitNs)) {
+    int s = 0;
+    uint32_t phase = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (!mbar_wait_bounded(&full[s], phase, kWaitLimitNs)) {
             if (lane == 0) record_error(status, kDevErrTmaTimeout);
-            mbar_wait_bounded(&full[s], use & 1, kDrainLimitNs);
+            mbar_wait_bounded(&full[s], phase, kDrainLimitNs);
             return;
         }
         const TileRec rec = info[s];
@@ -327,6 +329,10 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
     }
 }
 

@@ -193,12 +193,11 @@ hwc_kernel(const __grid_constant__ HwcDesc d, int64_t ntiles, int *status)
     if (warp == NC) {
         if (lane != 0) return;
         int64_t issued = 0;
-        for (int64_t i = 0;; ++i) {
-            const int64_t t = blockIdx.x + i * static_cast<int64_t>(gridDim.x);
-            if (t >= ntiles) break;
-            const int s = static_cast<int>(i % S);
-            const uint32_t use = static_cast<uint32_t>(i / S);
-            if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1, kWaitLimitNs)) {
+        int s = 0;             // stage of this tile
+        uint32_t phase = 0;    // parity of the stage's current use
+        bool wrapped = false;  // every stage has been used once
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if (wrapped && !mbar_wait_bounded(&empty[s], phase ^ 1u, kWaitLimitNs)) {
                 record_error(status, kDevErrTmaTimeout);
                 break;
             }
@@ -210,6 +209,11 @@ hwc_kernel(const __grid_constant__ HwcDesc d, int64_t ntiles, int *status)
             tma_load_3d(dst, &d.tmap, &full[s], x0, ty * TH, 0);
             tma_load_3d(dst + BOXB, &d.tmap, &full[s], x0 + kHwcBoxBOffset * kHwcPlanes, ty * TH, 0);
             ++issued;
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
+                wrapped = true;
+            }
         }
         for (int64_t j = (issued > S ? issued - S : 0); j < issued; ++j)
             mbar_wait_bounded(&full[j % S], static_cast<uint32_t>(j / S) & 1, kDrainLimitNs);
@@ -223,14 +227,12 @@ hwc_kernel(const __grid_constant__ HwcDesc d, int64_t ntiles, int *status)
     const bool scaled = d.oscale != 1.f;
     const int half = lane >> 4;              // 0: box A, 1: box B
     const int lpx = 4 * (lane & 15);         // first pixel of the lane inside its box
-    for (int64_t i = 0;; ++i) {
-        const int64_t t = blockIdx.x + i * static_cast<int64_t>(gridDim.x);
-        if (t >= ntiles) break;
-        const int s = static_cast<int>(i % S);
-        const uint32_t use = static_cast<uint32_t>(i / S);
-        if (!mbar_wait_bounded(&full[s], use & 1, kWaitLimitNs)) {
+    int s = 0;
+    uint32_t phase = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (!mbar_wait_bounded(&full[s], phase, kWaitLimitNs)) {
             if (lane == 0) record_error(status, kDevErrTmaTimeout);
-            mbar_wait_bounded(&full[s], use & 1, kDrainLimitNs);
+            mbar_wait_bounded(&full[s], phase, kDrainLimitNs);
             return;
         }
         const int ty = static_cast<int>(t / d.tiles_x);
@@ -248,6 +250,10 @@ hwc_kernel(const __grid_constant__ HwcDesc d, int64_t ntiles, int *status)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
     }
 }
 
