@@ -241,7 +241,7 @@ struct sc5_plan_s {
     int device = 0;
     int shape_idx = 0;
     FusedShape shape{};
-    int ctas_per_sm = 1;
+    int ctas_per_sm = 0;
     float *T = nullptr;
     int64_t t_pitch = 0;
     // batch workspace (device + pinned staging), grown on demand
@@ -273,9 +273,10 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         *ctas = ov->ctas_per_sm;
     } else if (direct || taps != kTaps) {
         *idx = 0;
-        if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
+        *ctas = (ov && ov->ctas_per_sm) ? ov->ctas_per_sm : 0;  // 0: as many as fit
     } else {
         int th, tw, stg, c;
+        *ctas = 0;  // as many as fit, unless the table or the descriptor says otherwise
         if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &stg, &c)) {
             *idx = fused_find_shape(in_dtype, out_dtype, th, tw, stg);
             *ctas = c;

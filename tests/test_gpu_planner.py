@@ -1,0 +1,37 @@
+"""The planner's default launch configuration: without a tuning entry a plan
+uses the default shape at as many CTAs per SM as fit, which is never slower
+than an explicit single CTA per SM."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _time(sc5, plan, A, out, k, reps=10):
+    import torch
+    for _ in range(3):
+        plan.run(A, out, k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.run(A, out, k)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_default_uses_full_occupancy():
+    import torch
+    from paper_1711_09791_gb300 import sepconv5 as sc5
+    sc5.load()
+    sc5.autotune(0, [])
+    H = W = 4096
+    A = torch.zeros((3, H, W), dtype=torch.bfloat16, device="cuda")
+    out = torch.empty((3, H - 4, W - 4), dtype=torch.bfloat16, device="cuda")
+    k = [0.1, 0.2, 0.4, 0.2, 0.1]
+    th, tw, st = sc5.fused_configs("bf16")[0]
+    default = sc5.Plan(3, H, W, W, W - 4, "bf16")
+    one = sc5.Plan(3, H, W, W, W - 4, "bf16", tile_h=th, tile_w=tw, stages=st, ctas_per_sm=1)
+    t_default, t_one = _time(sc5, default, A, out, k), _time(sc5, one, A, out, k)
+    default.close()
+    one.close()
+    assert t_default <= t_one * 1.02, (t_default, t_one)
