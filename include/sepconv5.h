@@ -331,7 +331,11 @@ typedef struct {
 } sc5_serve_stats;
 
 /* Start a server on the current device: allocates its resident arena
- * (hbm_budget_bytes) and starts its scheduler and completion threads. */
+ * (hbm_budget_bytes) and starts its scheduler and completion threads.
+ * Host-side fault injection for tests, read from the environment here:
+ * SC5_SERVE_FAULT=arena_alloc makes the arena allocation fail (SC5_ENOMEM);
+ * SC5_SERVE_FAULT=sched_delay_ms=N makes the scheduler sleep N ms before
+ * each admission round.  Neither touches the GPU. */
 SC5_API sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out);
 
 /* Queue one request.  req->in and req->out are HOST pointers to

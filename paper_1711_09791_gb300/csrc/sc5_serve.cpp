@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -147,6 +148,7 @@ struct sc5_server_s {
     sc5_serve_stats stats{};
     std::thread sched, compl_;
     int next_stream = 0;
+    int fault_sched_delay_ms = 0;  // host-side fault injection (SC5_SERVE_FAULT)
 
     cudaEvent_t get_event()
     {
@@ -184,6 +186,11 @@ void sc5_server_s::scheduler_loop()
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         // 1. admission, in arrival order
+        if (fault_sched_delay_ms > 0 && !pending.empty()) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::milliseconds(fault_sched_delay_ms));
+            lk.lock();
+        }
         while (!pending.empty() && admitted < cfg.max_inflight) {
             auto r = pending.front();
             size_t in_off = 0, out_off = 0;
@@ -362,6 +369,13 @@ extern "C" sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out)
     if (!s) return fail(SC5_ENOMEM, "host allocation failed");
     s->cfg = *cfg;
     cudaGetDevice(&s->device);
+    // Host-side fault injection for tests (never touches the GPU):
+    //   SC5_SERVE_FAULT=arena_alloc       the arena allocation fails (SC5_ENOMEM)
+    //   SC5_SERVE_FAULT=sched_delay_ms=N  the scheduler sleeps N ms before each admission round
+    if (const char *f = std::getenv("SC5_SERVE_FAULT")) {
+        if (std::strcmp(f, "arena_alloc") == 0) return fail(SC5_ENOMEM, "injected fault: arena allocation failed");
+        if (std::strncmp(f, "sched_delay_ms=", 15) == 0) s->fault_sched_delay_ms = std::atoi(f + 15);
+    }
     cudaError_t e = cudaMalloc(&s->arena_base, cfg->hbm_budget_bytes);
     if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc of the serving arena");
     s->arena.reset(cfg->hbm_budget_bytes);
