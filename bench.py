@@ -341,7 +341,7 @@ def leg_batch(sc5, synth, oracle, stream, dtypes):
     scales = [448.0 / float(x.abs().max()) for x in x_dev]
     px = sum(h * w for h, w in shapes)
     t0 = time.perf_counter()
-    sc5.autotune(1, [(d, o) for d, o in dtypes])
+    sc5.autotune(2, [(d, o) for d, o in dtypes])
     tune_s = time.perf_counter() - t0
     results = {"workload": f"256 images, H and W log-uniform in [64,4096] (seed 3), {px / 1e6:.1f} Mpix x 3 planes",
                "autotune_s": round(tune_s, 1)}

@@ -124,11 +124,18 @@ __device__ __forceinline__ void store_row(uint64_t vL, uint64_t vR, uint64_t os2
 //   kk:  the taps as pairs (k[t], k[t]); os2 = (oscale, oscale)
 // Per element this is exactly hdot's sequence for the row pass (k0*a0, then
 // fused multiply-adds for t = 1..4), and the same sequence down the column.
-template <class TIn, class TOut, int R, int BW, int TAPS = kTaps>
+template <class TIn, class TOut, int R, int BW, int TAPS = kTaps, bool FULL = false>
 __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint64_t (&kk)[TAPS],
                                            uint64_t os2, bool scaled, TOut *__restrict__ out,
                                            int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
 {
+    // FULL: an interior strip (all R rows and 4 columns inside the image, vector
+    // stores aligned); the guards are then compile-time true.
+    if constexpr (FULL) {
+        rows_valid = R;
+        cols_valid = kColsPerThread;
+        vec = true;
+    }
     uint64_t accL[R], accR[R];
 #pragma unroll
     for (int r = 0; r < R + TAPS - 1; ++r) {
@@ -201,8 +208,25 @@ __device__ __forceinline__ void record_error(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// Which strip code a kernel instance runs, fixed per storage-format pair by
+// measurement on 3x8192x8192 images and the 256-image batch.  FP32 input is
+// HBM-bound: guarded strips only.  8/16-bit input is issue-bound: interior strips
+// run guard-free; a narrow output also caps registers so that three 288-thread
+// CTAs fit an SM (widths up to 7: width 9 would spill), and a batch with FP32 output keeps the guarded strips
+// (its many edge tiles measured faster there).
+template <class TIn, class TOut, bool BATCH>
+__host__ __device__ constexpr bool fast_strips()
+{
+    return sizeof(TIn) < 4 && (sizeof(TOut) < 4 || !BATCH);
+}
+template <class TIn, class TOut, int TH, int R, int TAPS>
+__host__ __device__ constexpr int min_ctas_per_sm()
+{
+    return (sizeof(TIn) < 4 && sizeof(TOut) < 4 && TH / R + 1 <= 9 && TAPS <= 7) ? 3 : 1;
+}
+
 template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH, bool DIRECT = false, int TAPS = kTaps>
-__global__ void __launch_bounds__(32 * (TH / R + 1), 1)
+__global__ void __launch_bounds__(32 * (TH / R + 1), (min_ctas_per_sm<TIn, TOut, TH, R, TAPS>()))
 fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__ descs,
              const TileRec *__restrict__ tiles, int64_t ntiles, int *status)
 {
@@ -322,10 +346,16 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
                              (warp * R) * BW + lane * kColsPerThread;
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
-            if constexpr (DIRECT)
+            if constexpr (DIRECT) {
                 conv_strip_direct<TIn, TOut, R, BW>(src, KK, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
-            else
-                conv_strip<TIn, TOut, R, BW, TAPS>(src, kk, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
+            } else {
+                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
+                    conv_strip<TIn, TOut, R, BW, TAPS, true>(src, kk, os2, scaled, dst, out_pitch, R,
+                                                             kColsPerThread, true);
+                else
+                    conv_strip<TIn, TOut, R, BW, TAPS, false>(src, kk, os2, scaled, dst, out_pitch, rows_valid,
+                                                              cols_valid, vec);
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
