@@ -572,8 +572,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         for n in (3, 7, 9):
             kn = synth.rng(100 + n).uniform(0, 1, n)
             kn = (kn / kn.sum()).astype(np.float32)
-            outn = torch.empty((P, H - n + 1, W - n + 1), dtype=torch.float32, device=dev)
-            pl = sepconv5.Plan(P, H, W, W, W - n + 1, taps=n)
+            # output rows padded to a multiple of 4 values (16 bytes): vector stores
+            opn = -(-(W - n + 1) // 4) * 4
+            outn = torch.empty((P, H - n + 1, opn), dtype=torch.float32, device=dev)
+            pl = sepconv5.Plan(P, H, W, W, opn, taps=n)
             msn, _ = timed(lambda: pl.run(A_dev, outn, kn, stream=stream), k2, 3)
             pl.close()
             algn = P * H * W * 4 + P * (H - n + 1) * (W - n + 1) * 4

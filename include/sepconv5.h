@@ -134,7 +134,10 @@ typedef struct {
     int32_t border;                /* sc5_border */
     int32_t algo;                  /* sc5_algo */
     int32_t tile_h, tile_w, stages;
-    int32_t ctas_per_sm;           /* 0 = as many as fit */
+    int32_t ctas_per_sm;           /* persistent CTAs per SM, capped at what fits; 0 =
+                                      the planner's choice: the tuning table's entry,
+                                      else the shape's measured default, else as many
+                                      as fit (HWC: as many as fit) */
     int64_t in_plane_stride, out_plane_stride;
     int32_t taps;                  /* kernel width: 0 or 5 (the paper's), or 3, 7, 9 */
     int32_t layout;                /* sc5_layout */

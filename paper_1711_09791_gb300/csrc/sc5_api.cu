@@ -273,15 +273,20 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         *ctas = ov->ctas_per_sm;
     } else if (direct || taps != kTaps) {
         *idx = 0;
-        *ctas = (ov && ov->ctas_per_sm) ? ov->ctas_per_sm : 0;  // 0: as many as fit
+        *ctas = (ov && ov->ctas_per_sm) ? ov->ctas_per_sm : fused_default_ctas(in_dtype, out_dtype, 0, direct, taps);
     } else {
         int th, tw, stg, c;
-        *ctas = 0;  // as many as fit, unless the table or the descriptor says otherwise
+        // the table's entry, else the shape's own default (0: as many as fit);
+        // the descriptor overrides either
+        *ctas = 0;
+        bool tuned = false;
         if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &stg, &c)) {
             *idx = fused_find_shape(in_dtype, out_dtype, th, tw, stg);
             *ctas = c;
+            tuned = *idx >= 0;
         }
         if (*idx < 0) *idx = 0;
+        if (!tuned) *ctas = fused_default_ctas(in_dtype, out_dtype, *idx);
         if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
     }
     const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx, direct, taps);
@@ -343,7 +348,7 @@ static sc5_status run_hwc(sc5_plan p, const void *in, void *out, const float *k,
     const float oscale = static_cast<float>(static_cast<double>(out_scale) / in_scale);
     hwc_fill(desc, m, out, d.out_pitch, Hv, Wv, p->shape.tile_h, k, oscale, vec);
     const int64_t ntiles = static_cast<int64_t>((Wv + 127) / 128) * ((Hv + p->shape.tile_h - 1) / p->shape.tile_h);
-    cudaError_t e = launch_hwc(d.in_dtype, d.out_dtype, desc, ntiles, s);
+    cudaError_t e = launch_hwc(d.in_dtype, d.out_dtype, desc, ntiles, d.ctas_per_sm, s);
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "HWC launch");
 }
 

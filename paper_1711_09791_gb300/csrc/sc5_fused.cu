@@ -70,6 +70,13 @@ int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int st
     return -1;
 }
 
+int fused_default_ctas(int in_dtype, int out_dtype, int idx, bool direct, int taps)
+{
+    const FusedEntry *e;
+    const int n = entries(in_dtype, out_dtype, &e, direct, taps);
+    return (idx >= 0 && idx < n) ? e[idx].ctas_default : 0;
+}
+
 int fused_threads(const FusedShape &s) { return 32 * (s.tile_h / s.rows_per_thread + 1); }
 
 // cudaFuncSetAttribute for the dynamic shared memory once per (function, device).

@@ -4,9 +4,11 @@
 
 namespace sc5 {
 
+// The default shape runs 2 CTAs per SM when untuned: on 3x8192x8192 BF16 it
+// measured 0.131 ms there against 0.149-0.150 ms at 1 or 3.
 #define SC5_SHAPES_16(TI, TO)                                   \
     {                                                           \
-        make_entry<TI, TO, 128, 128, 16, 2>(), /* default */    \
+        make_entry<TI, TO, 128, 128, 16, 2>(2), /* default */   \
         make_entry<TI, TO, 128, 128, 16, 3>(),                  \
         make_entry<TI, TO, 128, 128, 8, 4>(),                   \
         make_entry<TI, TO, 64, 128, 4, 6>(),                    \

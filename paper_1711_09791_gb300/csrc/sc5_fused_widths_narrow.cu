@@ -4,8 +4,10 @@
 
 namespace sc5 {
 
-// Other odd widths (3, 7, 9) of the separable kernel: one shape each.
-#define SC5_WIDTHS_16(TI, TO, N) {make_entry<TI, TO, 128, 128, 16, 2, false, N>()}
+// Other odd widths (3, 7, 9) of the separable kernel: one shape each.  Width 3
+// runs one CTA per SM when untuned (3x8192x8192 BF16: 0.142 ms against 0.154 ms
+// at 2 or more).
+#define SC5_WIDTHS_16(TI, TO, N) {make_entry<TI, TO, 128, 128, 16, 2, false, N>((N) == 3 ? 1 : 0)}
 
 int fused_width_entries_16(int in_dtype, int out_dtype, int taps, const FusedEntry **out)
 {

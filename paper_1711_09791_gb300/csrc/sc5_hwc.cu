@@ -314,7 +314,8 @@ int hwc_tile_h(int in_dtype, int out_dtype)
 
 int *status_word();  // sc5_fused.cu
 
-cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc_ptr, int64_t ntiles, cudaStream_t st)
+cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc_ptr, int64_t ntiles, int ctas_per_sm,
+                       cudaStream_t st)
 {
     HwcEntry e;
     if (!hwc_lookup(in_dtype, out_dtype, &e)) return cudaErrorInvalidValue;
@@ -336,6 +337,7 @@ cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc_ptr, int64_
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, e.fn, e.threads, e.smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const int64_t cap = static_cast<int64_t>(num_sms()) * per_sm;
     const int grid = static_cast<int>(ntiles < cap ? ntiles : cap);
     int *status = status_word();

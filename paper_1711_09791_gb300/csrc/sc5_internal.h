@@ -60,6 +60,8 @@ int fused_find_shape(int in_dtype, int out_dtype, int tile_h, int tile_w, int st
 int fused_threads(const FusedShape &s);
 // Max resident CTAs per SM for a shape (occupancy query), or <= 0 on error.
 int fused_max_ctas_per_sm(int in_dtype, int out_dtype, int idx, bool direct = false, int taps = 5);
+// CTAs per SM a shape runs when no tuning entry or descriptor names one (0: as many as fit).
+int fused_default_ctas(int in_dtype, int out_dtype, int idx, bool direct = false, int taps = 5);
 // Set the kernel attributes of a shape on the current device (call before
 // capturing a launch into a graph).
 cudaError_t fused_prepare(int in_dtype, int out_dtype, int idx, bool direct = false, int taps = 5);
@@ -77,7 +79,8 @@ int hwc_tile_h(int in_dtype, int out_dtype); // output rows per tile (0: pair no
 size_t hwc_desc_size();
 void hwc_fill(void *desc, const CUtensorMap &m, void *out, int64_t out_pitch, int Hv, int Wv, int tile_h,
               const float *k, float oscale, bool vec);
-cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc, int64_t ntiles, cudaStream_t st);
+// ctas_per_sm <= 0 or above what fits: as many CTAs per SM as fit.
+cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc, int64_t ntiles, int ctas_per_sm, cudaStream_t st);
 
 // Two-pass kernels and helpers (sc5_twopass.cu).
 cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int64_t in_pitch,

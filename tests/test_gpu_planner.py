@@ -1,6 +1,7 @@
 """The planner's default launch configuration: without a tuning entry a plan
-uses the default shape at as many CTAs per SM as fit, which is never slower
-than an explicit single CTA per SM."""
+uses the default shape at that shape's measured default CTAs per SM (as many
+as fit unless the shape names a count), which is never slower than an
+explicit single CTA per SM."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +20,7 @@ def _time(sc5, plan, A, out, k, reps=10):
     return e0.elapsed_time(e1) / reps
 
 
-def test_default_uses_full_occupancy():
+def test_default_not_slower_than_one_cta_per_sm():
     import torch
     from paper_1711_09791_gb300 import sepconv5 as sc5
     sc5.load()
