@@ -4,7 +4,7 @@
 #include <set>
 #include <utility>
 
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 

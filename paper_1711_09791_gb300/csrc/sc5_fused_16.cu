@@ -1,6 +1,6 @@
 // sc5_fused_16.cu -- fused-kernel instantiations for bfloat16 and binary16
 // storage (output in the same format or in FP32).
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 

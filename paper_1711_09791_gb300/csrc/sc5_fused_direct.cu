@@ -1,6 +1,6 @@
 // sc5_fused_direct.cu -- instantiations of the direct single-pass kernels
 // (general 5x5 matrix, 25 products per output) for every storage format.
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 

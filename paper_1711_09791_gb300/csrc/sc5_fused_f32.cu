@@ -1,5 +1,5 @@
 // sc5_fused_f32.cu -- fused-kernel instantiations for FP32 storage.
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 

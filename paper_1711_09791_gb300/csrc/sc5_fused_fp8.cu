@@ -1,6 +1,6 @@
 // sc5_fused_fp8.cu -- fused-kernel instantiations for FP8 E4M3 storage
 // (output in E4M3 or in FP32).
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 

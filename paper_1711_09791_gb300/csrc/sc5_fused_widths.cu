@@ -1,6 +1,6 @@
 // sc5_fused_widths.cu -- instantiations of the fused separable kernel for
 // the odd widths other than 5 (3, 7, 9), FP32 storage.
-#include "sc5_fused_impl.cuh"
+#include "sc5_fused_entry.cuh"
 
 namespace sc5 {
 
