@@ -457,7 +457,9 @@ def leg_serve(sc5, synth, n_req):
         return {"offered_req_s": round(rate, 1) if rate else None, "achieved_req_s": round(n / wall, 1),
                 "mpix_s": round(px_done[0] / wall / 1e6, 1), "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
                 "p99_ms": round(float(np.percentile(lat_ms, 99)), 3), "launches": st["launches"],
-                "merged_max": st["merged_max"], "resident_peak_bytes": st["resident_peak_bytes"]}
+                "merged_max": st["merged_max"], "resident_peak_bytes": st["resident_peak_bytes"],
+                "phases_ms": {f"{ph}_p{q}": round(st[f"{ph}_us_p{q}"] / 1e3, 3)
+                              for ph in ("queue", "stage", "run") for q in (50, 99)}}
 
     pool_bf = make_pool("bf16", 24)
     sat = run("bf16", True, 0.0, min(n_req, 2000), pool_bf, 11)

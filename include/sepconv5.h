@@ -331,6 +331,15 @@ typedef struct {
     uint64_t submitted, completed, launches, rejected;
     uint64_t merged_max;         /* largest number of requests in one launch */
     size_t resident_peak_bytes;  /* high-water mark of admitted buffers */
+    /* Where completed requests spent their time (microseconds, host clock,
+     * median and 99th percentile over the last 2^20 completions; 0 before the
+     * first):  queue = submitted until admitted (waiting for arena space or an
+     * in-flight slot; the input copy is enqueued at admission);  stage =
+     * admitted until its launch is enqueued (waiting for a compute-stream slot
+     * or the merge window);  run = launch enqueued until the completion thread
+     * sees the output copy done (input copy still in flight, kernel, output
+     * copy, polling). */
+    double queue_us_p50, queue_us_p99, stage_us_p50, stage_us_p99, run_us_p50, run_us_p99;
 } sc5_serve_stats;
 
 /* Start a server on the current device: allocates its resident arena

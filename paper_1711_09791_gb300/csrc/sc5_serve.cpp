@@ -19,6 +19,7 @@
 // launch, so a request's result is the same alone and in any mix.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstring>
@@ -102,10 +103,42 @@ struct Request {
     sc5_image img{};  // host pointers
     size_t in_bytes = 0, out_bytes = 0;
     size_t in_off = 0, out_off = 0;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_launch, t_done;
     cudaEvent_t h2d = nullptr;
     bool done = false;
     sc5_status status = SC5_OK;
+};
+
+// Phase durations of the last kPhaseLog completed requests (a ring).
+struct PhaseLog {
+    static constexpr size_t kPhaseLog = size_t(1) << 20;
+    std::vector<float> q, s, r;  // queue, stage, run (microseconds)
+    size_t n = 0;
+    static float us(Clock::duration d) { return std::chrono::duration<float, std::micro>(d).count(); }
+    void add(Clock::duration dq, Clock::duration ds, Clock::duration dr)
+    {
+        if (q.size() < kPhaseLog) {
+            q.push_back(us(dq));
+            s.push_back(us(ds));
+            r.push_back(us(dr));
+        } else {
+            const size_t i = n % kPhaseLog;
+            q[i] = us(dq);
+            s[i] = us(ds);
+            r[i] = us(dr);
+        }
+        ++n;
+    }
+    // p-th percentile (nearest rank) of a copy of v; 0 if empty.
+    static double pct(std::vector<float> v, double p)
+    {
+        if (v.empty()) return 0.0;
+        size_t k = static_cast<size_t>(std::ceil(p / 100.0 * v.size()));
+        k = k ? k - 1 : 0;
+        if (k >= v.size()) k = v.size() - 1;
+        std::nth_element(v.begin(), v.begin() + static_cast<std::ptrdiff_t>(k), v.end());
+        return v[k];
+    }
 };
 
 struct Launch {
@@ -149,6 +182,7 @@ struct sc5_server_s {
     std::thread sched, compl_;
     int next_stream = 0;
     int fault_sched_delay_ms = 0;  // host-side fault injection (SC5_SERVE_FAULT)
+    PhaseLog phases;
 
     cudaEvent_t get_event()
     {
@@ -202,6 +236,7 @@ void sc5_server_s::scheduler_loop()
             pending.pop_front();
             r->in_off = in_off;
             r->out_off = out_off;
+            r->t_admit = Clock::now();
             ++admitted;
             stats.resident_peak_bytes = std::max(stats.resident_peak_bytes, arena.used());
             r->h2d = get_event();
@@ -280,6 +315,8 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
     L.slot = slot;
     L.done = get_event();
     cudaStream_t cs = s_comp[s];
+    const auto t_launch = Clock::now();
+    for (auto &r : group) r->t_launch = t_launch;
     if (st == SC5_OK) {
         slot_busy[slot] = true;
         unsigned char *hs = slot_host + static_cast<size_t>(slot) * kSlotBytes;
@@ -330,6 +367,7 @@ void sc5_server_s::completion_loop()
                 if (q != cudaSuccess && r->status == SC5_OK) r->status = SC5_ECUDA;
                 r->t_done = now;
                 r->done = true;
+                phases.add(r->t_admit - r->t_submit, r->t_launch - r->t_admit, now - r->t_launch);
                 arena.release(r->in_off, r->in_bytes);
                 arena.release(r->out_off, r->out_bytes);
                 put_event(r->h2d);
@@ -462,8 +500,20 @@ extern "C" sc5_status serve_get_stats(sc5_server srv, sc5_serve_stats *stats)
 {
     clear_error();
     if (!srv || !stats) return fail(SC5_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(srv->mu);
-    *stats = srv->stats;
+    std::vector<float> q, s, r;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        *stats = srv->stats;
+        q = srv->phases.q;
+        s = srv->phases.s;
+        r = srv->phases.r;
+    }
+    stats->queue_us_p50 = PhaseLog::pct(q, 50);
+    stats->queue_us_p99 = PhaseLog::pct(q, 99);
+    stats->stage_us_p50 = PhaseLog::pct(s, 50);
+    stats->stage_us_p99 = PhaseLog::pct(s, 99);
+    stats->run_us_p50 = PhaseLog::pct(r, 50);
+    stats->run_us_p99 = PhaseLog::pct(r, 99);
     return SC5_OK;
 }
 

@@ -56,7 +56,9 @@ class ServeCfg(ctypes.Structure):
 
 class ServeStats(ctypes.Structure):
     _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("launches", c_uint64),
-                ("rejected", c_uint64), ("merged_max", c_uint64), ("resident_peak_bytes", c_size_t)]
+                ("rejected", c_uint64), ("merged_max", c_uint64), ("resident_peak_bytes", c_size_t),
+                ("queue_us_p50", c_double), ("queue_us_p99", c_double), ("stage_us_p50", c_double),
+                ("stage_us_p99", c_double), ("run_us_p50", c_double), ("run_us_p99", c_double)]
 
 
 _lib = None

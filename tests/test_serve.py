@@ -121,6 +121,12 @@ def test_budget_bounds_resident_bytes(sc5):
     srv.close()
     assert stats["resident_peak_bytes"] <= budget
     assert stats["completed"] == 8
+    # phase times: ordered percentiles, and the requests beyond the budget waited
+    # in the queue for at least part of an earlier request's run
+    for ph in ("queue", "stage", "run"):
+        assert 0 <= stats[f"{ph}_us_p50"] <= stats[f"{ph}_us_p99"]
+    assert stats["run_us_p50"] > 0
+    assert stats["queue_us_p99"] >= 0.5 * stats["run_us_p50"], stats
 
 
 def test_refusals(sc5):
