@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed fused leg")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests per offered load")
-    ap.add_argument("--legs", default="c1,c3,c4,c5", help="extra configs to run beside the headline")
+    ap.add_argument("--legs", default="c1,c3,c4,paper,c5", help="extra configs to run beside the headline")
     return ap.parse_args()
 
 
@@ -282,6 +282,36 @@ def leg_c1(sc5, synth, stream):
     res["fused_graph_us"] = round(ms * 1e3, 2)
     b.close()
     plan.close()
+    return res
+
+
+# The paper's image sizes (3 planes of N x N) and its best two-pass time per
+# image with SIMD, OpenMP on the Xeon Phi 5110P (Table 2), for context only.
+PAPER_SIZES_MS = {1152: 0.8, 1728: 2.0, 2592: 4.1, 3888: 8.8, 5832: 19.6, 8748: 59.2}
+
+
+def leg_paper_sizes(sc5, stream):
+    """3 x N x N FP32 for the paper's six image sizes, fused and two-pass,
+    k = [1,4,6,4,1]/16, inputs uniform in [0, 255) drawn on the device
+    (seeded).  Below 3 x 2592^2 the image and its result fit in L2."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(4)
+    k = [1 / 16, 4 / 16, 6 / 16, 4 / 16, 1 / 16]
+    res = {"workload": "3xNxN f32, N in the paper's sizes, k=[1,4,6,4,1]/16",
+           "paper_ms_source": "Table 2, two-pass with SIMD, OpenMP, Xeon Phi 5110P"}
+    for n, paper_ms in PAPER_SIZES_MS.items():
+        A = torch.rand((P, n, n), generator=g, device="cuda") * 255.0
+        out = torch.empty((P, n - 4, n - 4), dtype=torch.float32, device="cuda")
+        row = {"paper_openmp_two_pass_ms": paper_ms}
+        for algo in ("fused", "two_pass"):
+            plan = sc5.Plan(P, n, n, n, n - 4, algo=algo)
+            ms = cuda_time(lambda: plan.run(A, out, k, stream=stream), 50, 5, stream)
+            plan.close()
+            row[f"{algo}_ms"] = round(ms, 5)
+        row["fused_mpix_s"] = round(n * n / (row["fused_ms"] / 1e3) / 1e6, 1)
+        res[str(n)] = row
+        del A, out
+    torch.cuda.empty_cache()
     return res
 
 
@@ -648,6 +678,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 pairs += [("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
                           ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
             extras["batch_c3_c4"] = leg_batch(sepconv5, synth, oracle, stream, pairs)
+        if "paper" in legs:
+            extras["paper_sizes"] = leg_paper_sizes(sepconv5, stream)
         if "c5" in legs:
             extras["serve_c5"] = leg_serve(sepconv5, synth, args.serve_requests)
     if rank != 0:

@@ -114,11 +114,17 @@ __device__ __forceinline__ void hwc_store_row(const uint64_t (&vL)[kHwcPlanes], 
     }
 }
 
-template <class TIn, class TOut, int R, int BW>
+template <class TIn, class TOut, int R, int BW, bool FULL = false>
 __device__ __forceinline__ void hwc_strip(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps], uint64_t os2,
                                           bool scaled, TOut *__restrict__ out, int64_t out_pitch, int rows_valid,
                                           int px_valid, bool vec)
 {
+    // FULL: all R rows and 4 pixels inside the image, vector stores aligned.
+    if constexpr (FULL) {
+        rows_valid = R;
+        px_valid = 4;
+        vec = true;
+    }
     uint64_t accL[R][kHwcPlanes], accR[R][kHwcPlanes];
 #pragma unroll
     for (int r = 0; r < R + kHalo; ++r) {
@@ -246,7 +252,14 @@ hwc_kernel(const __grid_constant__ HwcDesc d, int64_t ntiles, int *status)
                              (warp * R) * BW + lpx * kHwcPlanes;
             TOut *dst = reinterpret_cast<TOut *>(d.out) + static_cast<int64_t>(ry0) * d.out_pitch +
                         static_cast<int64_t>(px) * kHwcPlanes;
-            hwc_strip<TIn, TOut, R, BW>(src, kk, os2, scaled, dst, d.out_pitch, rows_valid, px_valid, d.vec != 0);
+            // guard-free interior strips for 8/16-bit in and out (3x8192^2: BF16
+            // 0.156 -> 0.152 ms, FP8 0.175 -> 0.163 ms); with FP32 output they
+            // measured 21% slower here, so those keep the guarded strips
+            if (sizeof(TIn) < 4 && sizeof(TOut) < 4 && rows_valid == R && px_valid == 4 && d.vec != 0)
+                hwc_strip<TIn, TOut, R, BW, true>(src, kk, os2, scaled, dst, d.out_pitch, R, 4, true);
+            else
+                hwc_strip<TIn, TOut, R, BW, false>(src, kk, os2, scaled, dst, d.out_pitch, rows_valid, px_valid,
+                                                   d.vec != 0);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
