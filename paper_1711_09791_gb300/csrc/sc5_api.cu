@@ -374,7 +374,6 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     if (!pair_supported(d.in_dtype, d.out_dtype))
         return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built: the output must be the input format or FP32",
                     d.in_dtype, d.out_dtype);
-    if (d.algo == SC5_ALGO_TWO_PASS && d.H > 65535) return fail(SC5_EINVAL, "two-pass form needs H <= 65535");
     sc5_plan p = new (std::nothrow) sc5_plan_s;
     if (!p) return fail(SC5_ENOMEM, "host allocation failed");
     p->d = d;
@@ -665,7 +664,6 @@ extern "C" sc5_status sepconv5_hpass(sc5_plan p, const void *in, float *T, int64
     if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
         return fail(SC5_EINVAL, "T needs t_pitch >= W-4, a multiple of 4, and 16-byte alignment");
     if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
-    if (d.H > 65535) return fail(SC5_EINVAL, "two-pass form needs H <= 65535");
     if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
     cudaError_t e = launch_hpass(d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch, T, t_pitch, k,
                                  static_cast<cudaStream_t>(stream), in_plane_of(d));

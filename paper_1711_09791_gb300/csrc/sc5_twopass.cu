@@ -11,6 +11,8 @@
 // (the paper's "two assignment operations", Sec. 7).  The arithmetic order is
 // the one of the fused kernel (hdot, then taps t = 0..4 of the column pass,
 // then the output scale), so both forms give identical bits.
+#include <algorithm>
+
 #include "sc5_device.cuh"
 
 namespace sc5 {
@@ -20,21 +22,14 @@ struct Taps {
 };
 
 constexpr int kPassThreads = 128;
-constexpr int kVRows = 8;  // output rows per thread in the vertical pass
+constexpr int kVRows = 8;          // output rows per thread in the vertical pass
+constexpr int kMaxGridYZ = 65535;  // grid y and z limit: rows and planes beyond it are strided
 
+// One row of the horizontal pass: 4 outputs from 8 inputs starting at `row`.
 template <class TIn>
-__global__ void __launch_bounds__(kPassThreads)
-hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t in_plane,
-             float *__restrict__ T, int64_t t_pitch, Taps taps)
+__device__ __forceinline__ void hpass_row(const TIn *__restrict__ row, int x, int W, int Wv, const float (&k)[kTaps],
+                                          float *__restrict__ dst)
 {
-    const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
-    const int Wv = W - kHalo;
-    if (x >= Wv) return;
-    const int y = blockIdx.y, p = blockIdx.z;
-    const TIn *row = in + p * in_plane + static_cast<int64_t>(y) * in_pitch + x;
-    float k[kTaps];
-#pragma unroll
-    for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
     float a[8];
     if (x + 8 <= W) {
         Fmt<TIn>::load8(row, a);
@@ -45,7 +40,6 @@ hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t
     float h[kColsPerThread];
 #pragma unroll
     for (int c = 0; c < kColsPerThread; ++c) h[c] = hdot(k, a + c);
-    float *dst = T + (static_cast<int64_t>(p) * H + y) * t_pitch + x;
     if (x + kColsPerThread <= Wv) {
         *reinterpret_cast<float4 *>(dst) = make_float4(h[0], h[1], h[2], h[3]);
     } else {
@@ -55,22 +49,31 @@ hpass_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t
     }
 }
 
-template <class TOut>
+
+template <class TIn>
 __global__ void __launch_bounds__(kPassThreads)
-vpass_kernel(const float *__restrict__ T, int H, int Wv, int64_t t_pitch, TOut *__restrict__ out,
-             int64_t out_pitch, int64_t out_plane, Taps taps, float oscale, int vec)
+hpass_kernel(const TIn *__restrict__ in, int P, int H, int W, int64_t in_pitch, int64_t in_plane,
+             float *__restrict__ T, int64_t t_pitch, Taps taps)
 {
     const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
+    const int Wv = W - kHalo;
     if (x >= Wv) return;
-    const int Hv = H - kHalo;
-    const int y0 = blockIdx.y * kVRows, p = blockIdx.z;
-    const int rows_valid = min(kVRows, Hv - y0);
-    const int cols_valid = min(kColsPerThread, Wv - x);
     float k[kTaps];
 #pragma unroll
     for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
-    const float *src = T + (static_cast<int64_t>(p) * H + y0) * t_pitch + x;
-    TOut *dst0 = out + p * out_plane + static_cast<int64_t>(y0) * out_pitch + x;
+    for (int p = blockIdx.z; p < P; p += gridDim.z)
+        for (int y = blockIdx.y; y < H; y += gridDim.y)
+            hpass_row<TIn>(in + p * in_plane + static_cast<int64_t>(y) * in_pitch + x, x, W, Wv, k,
+                           T + (static_cast<int64_t>(p) * H + y) * t_pitch + x);
+}
+
+// kVRows output rows of the vertical pass for one 4-column group: rows y0 ..
+// y0+kVRows+3 of T in, rows_valid of them out.
+template <class TOut>
+__device__ __forceinline__ void vpass_rows(const float *__restrict__ src, int H, int y0, int64_t t_pitch,
+                                           TOut *__restrict__ dst0, int64_t out_pitch, const float (&k)[kTaps],
+                                           float oscale, int vec, int rows_valid, int cols_valid)
+{
     float acc[kVRows][kColsPerThread];
 #pragma unroll
     for (int r = 0; r < kVRows + kHalo; ++r) {
@@ -105,15 +108,35 @@ vpass_kernel(const float *__restrict__ T, int H, int Wv, int64_t t_pitch, TOut *
     }
 }
 
+template <class TOut>
+__global__ void __launch_bounds__(kPassThreads)
+vpass_kernel(const float *__restrict__ T, int P, int H, int Wv, int64_t t_pitch, TOut *__restrict__ out,
+             int64_t out_pitch, int64_t out_plane, Taps taps, float oscale, int vec)
+{
+    const int x = (blockIdx.x * kPassThreads + threadIdx.x) * kColsPerThread;
+    if (x >= Wv) return;
+    const int Hv = H - kHalo;
+    const int cols_valid = min(kColsPerThread, Wv - x);
+    float k[kTaps];
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) k[t] = taps.k[t];
+    for (int p = blockIdx.z; p < P; p += gridDim.z)
+        for (int y0 = blockIdx.y * kVRows; y0 < Hv; y0 += gridDim.y * kVRows)
+            vpass_rows<TOut>(T + (static_cast<int64_t>(p) * H + y0) * t_pitch + x, H, y0, t_pitch,
+                             out + p * out_plane + static_cast<int64_t>(y0) * out_pitch + x, out_pitch, k, oscale,
+                             vec, min(kVRows, Hv - y0), cols_valid);
+}
+
 // The 2-pixel frame of a KEEP-border output: out = value(in) * ratio, stored
 // in the output format (an exact copy when formats and scales agree).
 template <class TIn, class TOut>
 __global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int64_t in_pitch, int64_t in_plane,
-                                  TOut *__restrict__ out, int64_t out_pitch, int64_t out_plane, float ratio, int rad)
+                                  TOut *__restrict__ out, int64_t out_pitch, int64_t out_plane, float ratio, int rad,
+                                  int P)
 {
     const int64_t n_rows = 2ll * rad * W;                    // rows 0..rad-1 and H-rad..H-1
     const int64_t n = n_rows + 2ll * rad * (H - 2 * rad);    // plus the first and last rad columns between
-    const int p = blockIdx.y;
+    for (int p = blockIdx.y; p < P; p += gridDim.y)
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         int y, x;
@@ -138,42 +161,45 @@ __global__ void keep_frame_kernel(const TIn *__restrict__ in, int H, int W, int6
 // (2 elements = half a group keeps both halves aligned).
 template <class T, class Half, class Group>
 __global__ void copy_interior_kernel(const T *__restrict__ src, int64_t src_pitch, int64_t src_plane,
-                                     T *__restrict__ dst, int64_t dst_pitch, int64_t dst_plane, int cols)
+                                     T *__restrict__ dst, int64_t dst_pitch, int64_t dst_plane, int P, int rows,
+                                     int cols)
 {
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (x >= cols) return;
-    const int y = blockIdx.y, p = blockIdx.z;
-    const T *s = src + p * src_plane + static_cast<int64_t>(y) * src_pitch + x;
-    T *d = dst + p * dst_plane + static_cast<int64_t>(y) * dst_pitch + x;
-    if (x + 4 <= cols) {
-        const Group g = *reinterpret_cast<const Group *>(s);
-        const Half *h = reinterpret_cast<const Half *>(&g);
-        reinterpret_cast<Half *>(d)[0] = h[0];
-        reinterpret_cast<Half *>(d)[1] = h[1];
-    } else {
-        for (int c = 0; x + c < cols; ++c) d[c] = s[c];
-    }
+    for (int p = blockIdx.z; p < P; p += gridDim.z)
+        for (int y = blockIdx.y; y < rows; y += gridDim.y) {
+            const T *s = src + p * src_plane + static_cast<int64_t>(y) * src_pitch + x;
+            T *d = dst + p * dst_plane + static_cast<int64_t>(y) * dst_pitch + x;
+            if (x + 4 <= cols) {
+                const Group g = *reinterpret_cast<const Group *>(s);
+                const Half *h = reinterpret_cast<const Half *>(&g);
+                reinterpret_cast<Half *>(d)[0] = h[0];
+                reinterpret_cast<Half *>(d)[1] = h[1];
+            } else {
+                for (int c = 0; x + c < cols; ++c) d[c] = s[c];
+            }
+        }
 }
 
 cudaError_t launch_copy_interior(int dtype, const void *src, int64_t src_pitch, int64_t src_plane, void *dst,
                                  int64_t dst_pitch, int64_t dst_plane, int P, int rows, int cols, cudaStream_t st)
 {
-    const dim3 grid((cols / 4 + 1 + 127) / 128, rows, P);
+    const dim3 grid((cols / 4 + 1 + 127) / 128, std::min(rows, kMaxGridYZ), std::min(P, kMaxGridYZ));
     switch (dtype) {
     case SC5_F32:
         copy_interior_kernel<float, float2, float4><<<grid, 128, 0, st>>>(
-            static_cast<const float *>(src), src_pitch, src_plane, static_cast<float *>(dst), dst_pitch, dst_plane, cols);
+            static_cast<const float *>(src), src_pitch, src_plane, static_cast<float *>(dst), dst_pitch, dst_plane, P, rows, cols);
         break;
     case SC5_BF16:
     case SC5_F16:
         copy_interior_kernel<uint16_t, uint32_t, uint2><<<grid, 128, 0, st>>>(
             static_cast<const uint16_t *>(src), src_pitch, src_plane, static_cast<uint16_t *>(dst), dst_pitch,
-            dst_plane, cols);
+            dst_plane, P, rows, cols);
         break;
     case SC5_FP8E4M3:
         copy_interior_kernel<uint8_t, uint16_t, uint32_t><<<grid, 128, 0, st>>>(
             static_cast<const uint8_t *>(src), src_pitch, src_plane, static_cast<uint8_t *>(dst), dst_pitch,
-            dst_plane, cols);
+            dst_plane, P, rows, cols);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -199,20 +225,20 @@ cudaError_t launch_hpass(int in_dtype, const void *in, int P, int H, int W, int6
     if (in_plane <= 0) in_plane = static_cast<int64_t>(H) * in_pitch;
     const int Wv = W - kHalo;
     const int groups = (Wv + kColsPerThread - 1) / kColsPerThread;
-    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, H, P);
+    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, std::min(H, kMaxGridYZ), std::min(P, kMaxGridYZ));
     const Taps taps = make_taps(k);
     switch (in_dtype) {
     case SC5_F32:
-        hpass_kernel<float><<<grid, kPassThreads, 0, st>>>(static_cast<const float *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
+        hpass_kernel<float><<<grid, kPassThreads, 0, st>>>(static_cast<const float *>(in), P, H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_BF16:
-        hpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const bf16_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
+        hpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const bf16_t *>(in), P, H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_F16:
-        hpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const f16_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
+        hpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(static_cast<const f16_t *>(in), P, H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     case SC5_FP8E4M3:
-        hpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(static_cast<const fp8e4m3_t *>(in), H, W, in_pitch, in_plane, T, t_pitch, taps);
+        hpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(static_cast<const fp8e4m3_t *>(in), P, H, W, in_pitch, in_plane, T, t_pitch, taps);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -227,21 +253,22 @@ cudaError_t launch_vpass(int out_dtype, const float *T, int P, int H, int Wv, in
 {
     const int Hv = H - kHalo;
     const int groups = (Wv + kColsPerThread - 1) / kColsPerThread;
-    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, (Hv + kVRows - 1) / kVRows, P);
+    const dim3 grid((groups + kPassThreads - 1) / kPassThreads, std::min((Hv + kVRows - 1) / kVRows, kMaxGridYZ),
+                    std::min(P, kMaxGridYZ));
     const Taps taps = make_taps(k);
     const int v = vec ? 1 : 0;
     switch (out_dtype) {
     case SC5_F32:
-        vpass_kernel<float><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<float *>(out), out_pitch, out_plane, taps, oscale, v);
+        vpass_kernel<float><<<grid, kPassThreads, 0, st>>>(T, P, H, Wv, t_pitch, static_cast<float *>(out), out_pitch, out_plane, taps, oscale, v);
         break;
     case SC5_BF16:
-        vpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<bf16_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        vpass_kernel<bf16_t><<<grid, kPassThreads, 0, st>>>(T, P, H, Wv, t_pitch, static_cast<bf16_t *>(out), out_pitch, out_plane, taps, oscale, v);
         break;
     case SC5_F16:
-        vpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<f16_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        vpass_kernel<f16_t><<<grid, kPassThreads, 0, st>>>(T, P, H, Wv, t_pitch, static_cast<f16_t *>(out), out_pitch, out_plane, taps, oscale, v);
         break;
     case SC5_FP8E4M3:
-        vpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(T, H, Wv, t_pitch, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, taps, oscale, v);
+        vpass_kernel<fp8e4m3_t><<<grid, kPassThreads, 0, st>>>(T, P, H, Wv, t_pitch, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, taps, oscale, v);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -255,12 +282,12 @@ static cudaError_t frame_out(int out_dtype, const TIn *in, int P, int H, int W, 
                              void *out, int64_t out_pitch, int64_t out_plane, float ratio, cudaStream_t st, int rad)
 {
     const int64_t n = 2ll * rad * W + 2ll * rad * (H - 2 * rad);
-    const dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), P);
+    const dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), std::min(P, kMaxGridYZ));
     switch (out_dtype) {
-    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<float *>(out), out_pitch, out_plane, ratio, rad); break;
-    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<bf16_t *>(out), out_pitch, out_plane, ratio, rad); break;
-    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<f16_t *>(out), out_pitch, out_plane, ratio, rad); break;
-    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, ratio, rad); break;
+    case SC5_F32: keep_frame_kernel<TIn, float><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<float *>(out), out_pitch, out_plane, ratio, rad, P); break;
+    case SC5_BF16: keep_frame_kernel<TIn, bf16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<bf16_t *>(out), out_pitch, out_plane, ratio, rad, P); break;
+    case SC5_F16: keep_frame_kernel<TIn, f16_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<f16_t *>(out), out_pitch, out_plane, ratio, rad, P); break;
+    case SC5_FP8E4M3: keep_frame_kernel<TIn, fp8e4m3_t><<<grid, 256, 0, st>>>(in, H, W, in_pitch, in_plane, static_cast<fp8e4m3_t *>(out), out_pitch, out_plane, ratio, rad, P); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
