@@ -164,44 +164,9 @@ __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint
     }
 }
 
-// One lane's strip, direct form (the single-pass algorithm of Sec. 5.1 with
-// a general 5x5 matrix): every output is one FP32 chain of 25 products in the
-// row-major order of Eq. 3, K[0][0]*A[y][x] first, then fused multiply-adds
-// through K[4][4]*A[y+4][x+4].  KK holds the 25 entries as pairs (K, K).
-template <class TIn, class TOut, int R, int BW>
-__device__ __forceinline__ void conv_strip_direct(const TIn *__restrict__ s, const uint64_t (&KK)[kTaps * kTaps],
-                                                  uint64_t os2, bool scaled, TOut *__restrict__ out,
-                                                  int64_t out_pitch, int rows_valid, int cols_valid, bool vec)
-{
-    uint64_t accL[R], accR[R];
-#pragma unroll
-    for (int r = 0; r < R + kHalo; ++r) {
-        uint64_t PL[kTaps], PR[kTaps];
-        row_pairs<TIn>(s + r * BW, PL, PR);
-        // input row r is kernel row i = r - o of output row o
-#pragma unroll
-        for (int i = 0; i < kTaps; ++i) {
-            const int o = r - i;
-            if (o >= 0 && o < R) {
-#pragma unroll
-                for (int j = 0; j < kTaps; ++j) {
-                    const uint64_t Kij = KK[i * kTaps + j];
-                    if (i == 0 && j == 0) {
-                        accL[o] = mul2(Kij, PL[0]);
-                        accR[o] = mul2(Kij, PR[0]);
-                    } else {
-                        accL[o] = fma2(Kij, PL[j], accL[o]);
-                        accR[o] = fma2(Kij, PR[j], accR[o]);
-                    }
-                }
-            }
-        }
-        const int o = r - kHalo;
-        if (o >= 0 && o < rows_valid)
-            store_row<TIn, TOut>(accL[o], accR[o], os2, scaled, out + static_cast<int64_t>(o) * out_pitch,
-                                 cols_valid, vec);
-    }
-}
+// The direct form's strip (sc5_fused_direct_strip.cuh) uses row_pairs and
+// store_row above.
+#include "sc5_fused_direct_strip.cuh"
 
 __device__ __forceinline__ void record_error(int *status, int code)
 {
@@ -347,7 +312,12 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
             if constexpr (DIRECT) {
-                conv_strip_direct<TIn, TOut, R, BW>(src, KK, os2, scaled, dst, out_pitch, rows_valid, cols_valid, vec);
+                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
+                    conv_strip_direct<TIn, TOut, R, BW, true>(src, KK, os2, scaled, dst, out_pitch, R,
+                                                              kColsPerThread, true);
+                else
+                    conv_strip_direct<TIn, TOut, R, BW, false>(src, KK, os2, scaled, dst, out_pitch, rows_valid,
+                                                               cols_valid, vec);
             } else {
                 if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
                     conv_strip<TIn, TOut, R, BW, TAPS, true>(src, kk, os2, scaled, dst, out_pitch, R,

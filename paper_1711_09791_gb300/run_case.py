@@ -17,7 +17,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16", "fp8e4m3"])
     ap.add_argument("--out", default=None, help="output format (default: the input format)")
-    ap.add_argument("--algo", default="fused", choices=["fused", "two_pass"])
+    ap.add_argument("--algo", default="fused", choices=["fused", "two_pass", "direct"])
     ap.add_argument("--planes", type=int, default=3)
     ap.add_argument("--H", type=int, default=8192)
     ap.add_argument("--W", type=int, default=8192)
