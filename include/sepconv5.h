@@ -169,6 +169,13 @@ typedef struct {
  * workspace cannot be allocated.  Calls cudaMalloc on the current device. */
 SC5_API sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out);
 SC5_API sc5_status sepconv5_plan_destroy(sc5_plan plan);
+/* The launch configuration a plan chose (from the descriptor, the tuning
+ * table or the defaults): fused tile rows and columns, pipeline stages, and
+ * CTAs per SM (0 where the kernel takes as many as fit, e.g. HWC plans).
+ * Any output pointer may be NULL.  Two-pass plans report the fused shape
+ * they would use. */
+SC5_API sc5_status sepconv5_plan_info(sc5_plan plan, int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                      int32_t *ctas_per_sm);
 
 /* Run the plan on one image: in (dev, in_dtype, [planes][H][in_pitch]),
  * out (dev, out_dtype, layout per border), k (host, the plan's taps values --
@@ -294,10 +301,11 @@ SC5_API sc5_status sepconv5_fused_configs(int32_t in_dtype, int32_t out_dtype, i
                                   int32_t cap, int32_t *n);
 
 /* Autotuner (the counterpart of the paper's thread/task-count tuning, Sec. 4
- * and Sec. 7): for every size class (log2 of the plane area, 6 classes from
- * 2^12 to 2^26 pixels) and dtype pair in `dtypes` (pairs in, out), time every
- * compiled shape and CTA count on synthetic images on the current device and
- * keep the fastest.  mode: 0 = off (built-in defaults), 1 = quick (one size
+ * and Sec. 7): for every size class (log2 of the plane area, 7 classes from
+ * below 2^14 to 2^24 pixels and above), dtype pair in `dtypes` (pairs in, out)
+ * and kernel kind (the single-image kernel of plans; the work-list kernel of
+ * batches and merged serving launches), time every compiled shape and CTA
+ * count on synthetic images on the current device and keep the fastest.  mode: 0 = off (built-in defaults), 1 = quick (one size
  * per class), 2 = full.  The table is kept in the process and, if path is
  * not NULL, written there as JSON keyed by GPU name.  Allocates device memory
  * for its test images. */
@@ -305,10 +313,17 @@ SC5_API sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int32_
                              const char *path);
 /* Load a table written by sepconv5_autotune (entries for other GPUs are ignored). */
 SC5_API sc5_status sepconv5_tune_load(const char *path);
-/* The shape the planner would pick for a plane of H x W with these dtypes. */
+/* The shape a plan would pick for a plane of H x W with these dtypes:
+ * SC5_OK with the tuned entry, or SC5_ENOTFOUND with the default shape and
+ * ctas_per_sm = 0 when the table has none. */
 SC5_API sc5_status sepconv5_tune_lookup(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
                                 int32_t *tile_h, int32_t *tile_w, int32_t *stages,
                                 int32_t *ctas_per_sm);
+/* The same for a batch (or merged serving launch) whose dominant size class
+ * is that of an H x W plane. */
+SC5_API sc5_status sepconv5_tune_lookup_batch(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
+                                      int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                      int32_t *ctas_per_sm);
 
 /* ---------------------------------------------------------------- serving */
 

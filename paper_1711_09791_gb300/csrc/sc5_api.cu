@@ -262,7 +262,7 @@ struct sc5_plan_s {
 
 namespace sc5 {
 sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
-                        bool direct, int taps)
+                        bool direct, int taps, bool batch)
 {
     if (ov && (ov->tile_h || ov->tile_w || ov->stages)) {
         const int i = fused_find_shape(in_dtype, out_dtype, ov->tile_h ? ov->tile_h : 64,
@@ -280,7 +280,7 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         // the descriptor overrides either
         *ctas = 0;
         bool tuned = false;
-        if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &stg, &c)) {
+        if (tune_lookup_internal(in_dtype, out_dtype, H, W, batch ? kKindBatch : kKindSingle, &th, &tw, &stg, &c)) {
             *idx = fused_find_shape(in_dtype, out_dtype, th, tw, stg);
             *ctas = c;
             tuned = *idx >= 0;
@@ -400,6 +400,18 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
         return fail(SC5_ECUDA, "cudaEventCreate failed");
     }
     *out = p;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_plan_info(sc5_plan p, int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                         int32_t *ctas_per_sm)
+{
+    clear_error();
+    if (!p) return fail(SC5_EINVAL, "null plan");
+    if (tile_h) *tile_h = p->shape.tile_h;
+    if (tile_w) *tile_w = p->shape.tile_w;
+    if (stages) *stages = p->shape.stages;
+    if (ctas_per_sm) *ctas_per_sm = p->ctas_per_sm;
     return SC5_OK;
 }
 
@@ -754,7 +766,7 @@ sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_imag
     const int side = 1 << (best / 2);
     const int H = side, W = (best % 2) ? side * 2 : side;
     *idx = -1;
-    return choose_shape(in_dtype, out_dtype, H, W, nullptr, idx, ctas);
+    return choose_shape(in_dtype, out_dtype, H, W, nullptr, idx, ctas, false, kTaps, true);
 }
 
 // Shape for a batch: the plan's override, else the tuned choice for the size

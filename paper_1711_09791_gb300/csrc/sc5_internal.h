@@ -104,9 +104,11 @@ int num_sms();
 sc5_status fail(sc5_status st, const char *fmt, ...);
 sc5_status fail_cuda(cudaError_t e, const char *what);
 void clear_error();
-// Fused shape and CTAs/SM for a plane size (override > tuned table > default).
+// Fused shape and CTAs/SM for a plane size (override > tuned table > default);
+// `batch` selects the tuning entries of the work-list kernel (batches, merged
+// serving launches) instead of those of the single-image kernel.
 sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_plan_desc *ov, int *idx, int *ctas,
-                        bool direct = false, int taps = kTaps);
+                        bool direct = false, int taps = kTaps, bool batch = false);
 // Shape for a set of images: tuned choice for the size class with most pixels.
 sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas);
 // Host image of a batch launch: ImgDesc[n] then (256-byte aligned) TileRec[tiles].

@@ -1,11 +1,13 @@
 // sc5_tune.cu -- autotuner for the fused kernel (the GPU counterpart of the
 // paper's tuning of the thread / task count, Sec. 4 and Sec. 7: 100 threads
 // was the chosen "magic number", 120 helped some images).  For each size
-// class of plane area and each dtype pair it times every compiled tile shape
-// at every feasible CTAs-per-SM count on a batch of synthetic images of that
-// class (at least 512 MB of input, replayed from a CUDA graph) and keeps the
-// fastest.  The table lives in the process and can be saved / loaded as JSON
-// (one entry per line) keyed by GPU name.
+// class of plane area, each dtype pair and each kernel kind it times every
+// compiled tile shape at every feasible CTAs-per-SM count on synthetic images
+// of that class and keeps the fastest: the batch kind on a batch of at least
+// 512 MB of input replayed from a CUDA graph, the single-image kind on up to
+// 32 separate plan runs over distinct images of the same set.  The table
+// lives in the process and can be saved / loaded as JSON (one entry per
+// line) keyed by GPU name.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -24,7 +26,7 @@ sc5_status fail_cuda(cudaError_t e, const char *what);
 void clear_error();
 
 struct TuneEntry {
-    int in, out, cls;
+    int in, out, kind, cls;
     int th, tw, stages, ctas;
     double us;
 };
@@ -47,13 +49,13 @@ static void class_shape(int c, int *H, int *W)
     *W = 1 << (e - e / 2);
 }
 
-bool tune_lookup_internal(int in_dtype, int out_dtype, int H, int W, int *tile_h, int *tile_w, int *stages,
-                          int *ctas_per_sm)
+bool tune_lookup_internal(int in_dtype, int out_dtype, int H, int W, int kind, int *tile_h, int *tile_w,
+                          int *stages, int *ctas_per_sm)
 {
     const int c = size_class(static_cast<double>(H) * W);
     std::lock_guard<std::mutex> lk(g_mu);
     for (const auto &e : g_table)
-        if (e.in == in_dtype && e.out == out_dtype && e.cls == c) {
+        if (e.in == in_dtype && e.out == out_dtype && e.kind == kind && e.cls == c) {
             *tile_h = e.th;
             *tile_w = e.tw;
             *stages = e.stages;
@@ -72,11 +74,15 @@ static std::string gpu_name()
     return prop.name;
 }
 
-// Median time in microseconds of `reps` replays of one configuration on a
-// batch of n images of one size (a graph-captured batch launch).
-static sc5_status time_config(int in, int out, int H, int W, int n, int idx, int ctas, unsigned char *din,
-                              unsigned char *dout, size_t in_img, size_t out_img, int reps, double *us)
+// Median time in microseconds of `reps` repetitions of one configuration on
+// n images of one size: one graph-replayed batch launch (batch kind), or one
+// plan run per image for up to kSingleRuns images (single-image kind, time
+// per run scaled to n images).
+static sc5_status time_config(int in, int out, int H, int W, int n, int idx, int ctas, int kind,
+                              unsigned char *din, unsigned char *dout, size_t in_img, size_t out_img, int reps,
+                              double *us)
 {
+    constexpr int kSingleRuns = 32;
     FusedShape sh;
     fused_shape(in, out, idx, &sh);
     sc5_plan_desc d{};
@@ -111,11 +117,14 @@ static sc5_status time_config(int in, int out, int H, int W, int n, int idx, int
         im.in_scale = im.out_scale = 1.f;
     }
     sc5_batch b = nullptr;
-    st = sepconv5_batch_create(p, n, imgs.data(), &b);
-    if (st != SC5_OK) {
-        sepconv5_plan_destroy(p);
-        return st;
+    if (kind == kKindBatch) {
+        st = sepconv5_batch_create(p, n, imgs.data(), &b);
+        if (st != SC5_OK) {
+            sepconv5_plan_destroy(p);
+            return st;
+        }
     }
+    const int runs = std::min(n, kSingleRuns);
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     cudaEvent_t a, e;
@@ -124,17 +133,23 @@ static sc5_status time_config(int in, int out, int H, int W, int n, int idx, int
     std::vector<float> ts;
     for (int r = 0; r < reps + 2 && st == SC5_OK; ++r) {
         cudaEventRecord(a, s);
-        st = sepconv5_batch_launch(b, s);
+        if (kind == kKindBatch) {
+            st = sepconv5_batch_launch(b, s);
+        } else {
+            for (int i = 0; i < runs && st == SC5_OK; ++i)
+                st = sepconv5_run(p, imgs[i].in, imgs[i].out, imgs[i].k, 1.f, 1.f, s);
+        }
         cudaEventRecord(e, s);
         cudaEventSynchronize(e);
         float ms = 0;
         cudaEventElapsedTime(&ms, a, e);
+        if (kind != kKindBatch) ms *= static_cast<float>(n) / runs;
         if (r >= 2) ts.push_back(ms);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(e);
     cudaStreamDestroy(s);
-    sepconv5_batch_destroy(b);
+    if (b) sepconv5_batch_destroy(b);
     sepconv5_plan_destroy(p);
     if (st != SC5_OK) return st;
     std::sort(ts.begin(), ts.end());
@@ -152,9 +167,9 @@ static sc5_status save_table(const char *path)
     for (size_t i = 0; i < g_table.size(); ++i) {
         const auto &e = g_table[i];
         std::fprintf(f,
-                     "{\"in\": %d, \"out\": %d, \"cls\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, "
-                     "\"ctas\": %d, \"us\": %.3f}%s\n",
-                     e.in, e.out, e.cls, e.th, e.tw, e.stages, e.ctas, e.us,
+                     "{\"in\": %d, \"out\": %d, \"kind\": %d, \"cls\": %d, \"tile_h\": %d, \"tile_w\": %d, "
+                     "\"stages\": %d, \"ctas\": %d, \"us\": %.3f}%s\n",
+                     e.in, e.out, e.kind, e.cls, e.th, e.tw, e.stages, e.ctas, e.us,
                      i + 1 < g_table.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
@@ -203,27 +218,30 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
                 cudaFree(dout);
                 return fail_cuda(e, "autotune buffers");
             }
-            TuneEntry best{in, out, c, 0, 0, 0, 0, 1e30};
-            for (int idx = 0; idx < nshapes; ++idx) {
-                const int maxc = fused_max_ctas_per_sm(in, out, idx);
-                for (int ctas = 1; ctas <= maxc; ++ctas) {
-                    double us = 0;
-                    sc5_status st = time_config(in, out, H, W, n, idx, ctas, din, dout, in_img, out_img, reps, &us);
-                    if (st != SC5_OK) {
-                        cudaFree(din);
-                        cudaFree(dout);
-                        return st;
-                    }
-                    if (us < best.us) {
-                        FusedShape sh;
-                        fused_shape(in, out, idx, &sh);
-                        best = TuneEntry{in, out, c, sh.tile_h, sh.tile_w, sh.stages, ctas, us};
+            for (int kind : {kKindSingle, kKindBatch}) {
+                TuneEntry best{in, out, kind, c, 0, 0, 0, 0, 1e30};
+                for (int idx = 0; idx < nshapes; ++idx) {
+                    const int maxc = fused_max_ctas_per_sm(in, out, idx);
+                    for (int ctas = 1; ctas <= maxc; ++ctas) {
+                        double us = 0;
+                        sc5_status st =
+                            time_config(in, out, H, W, n, idx, ctas, kind, din, dout, in_img, out_img, reps, &us);
+                        if (st != SC5_OK) {
+                            cudaFree(din);
+                            cudaFree(dout);
+                            return st;
+                        }
+                        if (us < best.us) {
+                            FusedShape sh;
+                            fused_shape(in, out, idx, &sh);
+                            best = TuneEntry{in, out, kind, c, sh.tile_h, sh.tile_w, sh.stages, ctas, us};
+                        }
                     }
                 }
+                found.push_back(best);
             }
             cudaFree(din);
             cudaFree(dout);
-            found.push_back(best);
         }
     }
     {
@@ -231,7 +249,8 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
         for (const auto &f : found) {
             g_table.erase(std::remove_if(g_table.begin(), g_table.end(),
                                          [&](const TuneEntry &e) {
-                                             return e.in == f.in && e.out == f.out && e.cls == f.cls;
+                                             return e.in == f.in && e.out == f.out && e.kind == f.kind &&
+                                                    e.cls == f.cls;
                                          }),
                           g_table.end());
             g_table.push_back(f);
@@ -258,9 +277,10 @@ extern "C" sc5_status sepconv5_tune_load(const char *path)
         }
         TuneEntry t;
         if (std::sscanf(line,
-                        " {\"in\": %d, \"out\": %d, \"cls\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, "
-                        "\"ctas\": %d, \"us\": %lf",
-                        &t.in, &t.out, &t.cls, &t.th, &t.tw, &t.stages, &t.ctas, &t.us) == 8)
+                        " {\"in\": %d, \"out\": %d, \"kind\": %d, \"cls\": %d, \"tile_h\": %d, \"tile_w\": %d, "
+                        "\"stages\": %d, \"ctas\": %d, \"us\": %lf",
+                        &t.in, &t.out, &t.kind, &t.cls, &t.th, &t.tw, &t.stages, &t.ctas, &t.us) == 9 &&
+            (t.kind == kKindSingle || t.kind == kKindBatch))
             loaded.push_back(t);
     }
     std::fclose(f);
@@ -272,14 +292,13 @@ extern "C" sc5_status sepconv5_tune_load(const char *path)
     return SC5_OK;
 }
 
-extern "C" sc5_status sepconv5_tune_lookup(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
-                                           int32_t *tile_h, int32_t *tile_w, int32_t *stages,
-                                           int32_t *ctas_per_sm)
+static sc5_status tune_lookup_kind(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W, int kind,
+                                   int32_t *tile_h, int32_t *tile_w, int32_t *stages, int32_t *ctas_per_sm)
 {
     clear_error();
     if (!tile_h || !tile_w || !stages || !ctas_per_sm) return fail(SC5_EINVAL, "null argument");
     int th, tw, st, c;
-    if (tune_lookup_internal(in_dtype, out_dtype, H, W, &th, &tw, &st, &c)) {
+    if (tune_lookup_internal(in_dtype, out_dtype, H, W, kind, &th, &tw, &st, &c)) {
         *tile_h = th;
         *tile_w = tw;
         *stages = st;
@@ -293,4 +312,18 @@ extern "C" sc5_status sepconv5_tune_lookup(int32_t in_dtype, int32_t out_dtype, 
     *stages = s.stages;
     *ctas_per_sm = 0;
     return SC5_ENOTFOUND;
+}
+
+extern "C" sc5_status sepconv5_tune_lookup(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
+                                           int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                           int32_t *ctas_per_sm)
+{
+    return tune_lookup_kind(in_dtype, out_dtype, H, W, kKindSingle, tile_h, tile_w, stages, ctas_per_sm);
+}
+
+extern "C" sc5_status sepconv5_tune_lookup_batch(int32_t in_dtype, int32_t out_dtype, int32_t H, int32_t W,
+                                                 int32_t *tile_h, int32_t *tile_w, int32_t *stages,
+                                                 int32_t *ctas_per_sm)
+{
+    return tune_lookup_kind(in_dtype, out_dtype, H, W, kKindBatch, tile_h, tile_w, stages, ctas_per_sm);
 }

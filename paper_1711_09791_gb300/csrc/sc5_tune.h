@@ -11,8 +11,15 @@ constexpr int kNumClasses = 7;
 // factor of 4 up to class 6 for >= 2^24.
 int size_class(double px);
 
-// Tuned choice for a dtype pair and plane size; false if the table has none.
-bool tune_lookup_internal(int in_dtype, int out_dtype, int H, int W, int *tile_h, int *tile_w,
+// Kernel kinds tuned separately: the single-image kernel of a plan and the
+// work-list kernel of batches and merged serving launches.  The same shape can
+// rank differently in the two (3x8192x8192 FP32, 64x128 tiles with 4 stages:
+// 0.287 ms single-image, 0.241 ms as a batch; with 3 stages 0.238 / 0.250 ms).
+constexpr int kKindSingle = 0, kKindBatch = 1;
+
+// Tuned choice for a dtype pair, plane size and kernel kind; false if the
+// table has none.
+bool tune_lookup_internal(int in_dtype, int out_dtype, int H, int W, int kind, int *tile_h, int *tile_w,
                           int *stages, int *ctas_per_sm);
 
 }  // namespace sc5

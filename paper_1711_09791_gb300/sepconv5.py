@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     sigs = {
         "sepconv5_plan": [POINTER(PlanDesc), POINTER(V)],
         "sepconv5_plan_destroy": [V],
+        "sepconv5_plan_info": [V, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)],
         "sepconv5_run": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_run_host": [V, V, V, POINTER(c_float), c_float, c_float, V],
         "sepconv5_run_K": [V, V, V, POINTER(c_float), c_float, c_float, V],
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         "sepconv5_autotune": [c_int32, POINTER(c_int32), c_int32, c_char_p],
         "sepconv5_tune_load": [c_char_p],
         "sepconv5_tune_lookup": [c_int32, c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32),
+                                 POINTER(c_int32), POINTER(c_int32)],
+        "sepconv5_tune_lookup_batch": [c_int32, c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32),
                                  POINTER(c_int32), POINTER(c_int32)],
         "serve_create": [POINTER(ServeCfg), POINTER(V)],
         "serve_submit": [V, POINTER(Image), POINTER(c_uint64)],
@@ -215,6 +218,12 @@ class Plan:
         _check(load().sepconv5_vpass(self._h, _ptr(T), t_pitch, _ptr(dst), _taps(k), in_scale, out_scale,
                                      _stream(stream)), "sepconv5_vpass")
 
+    def info(self) -> dict:
+        """The launch configuration the plan chose (sepconv5_plan_info)."""
+        th, tw, st, c = c_int32(), c_int32(), c_int32(), c_int32()
+        _check(load().sepconv5_plan_info(self._h, byref(th), byref(tw), byref(st), byref(c)), "sepconv5_plan_info")
+        return {"tile_h": th.value, "tile_w": tw.value, "stages": st.value, "ctas_per_sm": c.value}
+
     def run_batch(self, images, stream=None):
         arr = make_images(images)
         _check(load().sepconv5_run_batch(self._h, len(images), arr, _stream(stream)), "sepconv5_run_batch")
@@ -305,10 +314,13 @@ def tune_load(path: str):
     _check(load().sepconv5_tune_load(path.encode()), "sepconv5_tune_load")
 
 
-def tune_lookup(in_dtype, out_dtype, H, W) -> tuple[dict, bool]:
+def tune_lookup(in_dtype, out_dtype, H, W, batch: bool = False) -> tuple[dict, bool]:
+    """The tuned shape a plan (or, with batch=True, a batch) takes for an H x W
+    plane, and whether the table had an entry."""
     th, tw, st, c = c_int32(), c_int32(), c_int32(), c_int32()
-    s = load().sepconv5_tune_lookup(_dt(in_dtype), _dt(out_dtype), H, W, byref(th), byref(tw), byref(st), byref(c))
-    _check(s, "sepconv5_tune_lookup", ok=(OK, ENOTFOUND))
+    name = "sepconv5_tune_lookup_batch" if batch else "sepconv5_tune_lookup"
+    s = getattr(load(), name)(_dt(in_dtype), _dt(out_dtype), H, W, byref(th), byref(tw), byref(st), byref(c))
+    _check(s, name, ok=(OK, ENOTFOUND))
     return {"tile_h": th.value, "tile_w": tw.value, "stages": st.value, "ctas_per_sm": c.value}, s == OK
 
 

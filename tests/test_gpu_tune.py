@@ -17,26 +17,34 @@ def test_autotune_table_roundtrip(tmp_path):
     sc5.autotune(1, [("f32", "f32"), ("bf16", "bf16")], path)
     table = json.load(open(path))
     assert table["gpu"] == torch.cuda.get_device_name(0)
-    assert len(table["entries"]) == 2 * 7
+    assert len(table["entries"]) == 2 * 7 * 2  # pairs x size classes x kernel kinds
+    assert {e["kind"] for e in table["entries"]} == {0, 1}
     compiled = {p: set(sc5.fused_configs(*p)) for p in [("f32", "f32"), ("bf16", "bf16")]}
     for e in table["entries"]:
         pair = ({0: "f32", 1: "bf16"}[e["in"]], {0: "f32", 1: "bf16"}[e["out"]])
         assert (e["tile_h"], e["tile_w"], e["stages"]) in compiled[pair]
         assert e["ctas"] >= 1 and e["us"] > 0
     cfg, found = sc5.tune_lookup("f32", "f32", 8192, 8192)
-    assert found
+    cfgb, foundb = sc5.tune_lookup("f32", "f32", 8192, 8192, batch=True)
+    assert found and foundb
     sc5.autotune(0, [])  # clear
     assert not sc5.tune_lookup("f32", "f32", 8192, 8192)[1]
+    assert not sc5.tune_lookup("f32", "f32", 8192, 8192, batch=True)[1]
     sc5.tune_load(path)
     cfg2, found2 = sc5.tune_lookup("f32", "f32", 8192, 8192)
     assert found2 and cfg2 == cfg
+    assert sc5.tune_lookup("f32", "f32", 8192, 8192, batch=True) == (cfgb, True)
+    # a plan takes the single-image entry of its size class
+    plan1 = sc5.Plan(3, 8192, 8192)
+    assert plan1.info() == cfg
+    plan1.close()
     # a batch of large images takes the tuned shape of their size class
     A = torch.zeros((3, 3000, 3000), dtype=torch.float32, device="cuda")
     out = torch.zeros((3, 2996, 2996), dtype=torch.float32, device="cuda")
     plan = sc5.Plan(3, 64, 64)
     b = sc5.Batch(plan, [{"in": A, "out": out, "H": 3000, "W": 3000, "in_pitch": 3000, "out_pitch": 2996,
                           "k": [0, 0, 1, 0, 0]}])
-    want, _ = sc5.tune_lookup("f32", "f32", 2048, 4096)  # the dominant class of one 3000^2 image
+    want, _ = sc5.tune_lookup("f32", "f32", 2048, 4096, batch=True)  # the dominant class of one 3000^2 image
     info = b.info()
     assert (info["tile_h"], info["tile_w"]) == (want["tile_h"], want["tile_w"])
     b.launch()
