@@ -20,6 +20,10 @@ to it.  Each wrapper names the passage of the paper it follows:
 * :func:`decode`        -- exact decoding of bf16 / fp16 / fp8-e4m3 codes
 * :func:`keep_frame`    -- the "copy the 2-pixel frame" output (Listing 1's
                            in-place result, whose frame keeps the input)
+* :func:`reduce2`       -- one pyramid REDUCE step: Eq. 1 (K = k k^T) kept at
+                           every second row and column (the "scaling" of the
+                           stereo pipeline, Sec. 1, which the paper does not
+                           define: this is the reading taken)
 
 Output convention (the VALID region, Sec. 5: convolution starts at pixel
 (2,2) and the edges are ignored): plane p of the result is (H-4) x (W-4) and
@@ -72,6 +76,8 @@ def _bind(path: str):
     lib.sc5o_outer.argtypes = [P, P]
     lib.sc5o_direct_Kn.argtypes = [P, I, I, I, I, P, P]
     lib.sc5o_direct_Kn.restype = ctypes.c_int
+    lib.sc5o_reduce.argtypes = [P, I, I, I, P, P]
+    lib.sc5o_reduce.restype = ctypes.c_int
     for f in ("sc5o_direct_K", "sc5o_direct", "sc5o_hpass", "sc5o_vpass",
               "sc5o_points_f32", "sc5o_decode"):
         getattr(lib, f).restype = ctypes.c_int
@@ -156,6 +162,18 @@ def direct_n(A, k) -> np.ndarray:
     """Eq. 1 with K[i][j] = k[i] k[j] for a vector k of odd length n."""
     k = np.ascontiguousarray(k, dtype=np.float64).reshape(-1)
     return direct_Kn(A, np.outer(k, k))
+
+
+def reduce2(A, k) -> np.ndarray:
+    """One REDUCE step: [P][ceil((H-4)/2)][ceil((W-4)/2)] in FP64, output (y, x)
+    centred on input (2y+2, 2x+2)."""
+    A = _as3(A)
+    k = _k5(k)
+    P, H, W = A.shape
+    B = np.empty((P, (H - 3) // 2, (W - 3) // 2), np.float64)
+    if _load().sc5o_reduce(_ptr(A), P, H, W, _ptr(k), _ptr(B)) != 0:
+        raise ValueError("reduce2: image smaller than 5x5")
+    return B
 
 
 def hpass(A, k) -> np.ndarray:

@@ -180,6 +180,41 @@ int sc5o_direct_Kn(const double *A, int64_t P, int64_t H, int64_t W, int64_t n,
     return 0;
 }
 
+/*
+ * One REDUCE step of an image pyramid: Eq. 1 with K = k k^T kept at every
+ * second output row and column.  The paper names "convolution and scaling"
+ * as the two steps that take most of its stereo pipeline's time (Sec. 1) but
+ * does not define the scaling; the reading taken here is the blur-then-
+ * subsample step of a Gaussian pyramid on the VALID region:
+ *
+ *   B[p][y][x] = sum_i sum_j A[p][2y+i][2x+j] * k[i] * k[j]
+ *
+ * for y < Ho = ceil((H-4)/2), x < Wo = ceil((W-4)/2): output (y, x) is the
+ * VALID output (2y, 2x), centred on input (2y+2, 2x+2).  A is dense
+ * [P][H][W], B dense [P][Ho][Wo].
+ */
+int sc5o_reduce(const double *A, int64_t P, int64_t H, int64_t W,
+                const double k[SC5O_TAPS], double *B)
+{
+    if (P < 1 || H < SC5O_TAPS || W < SC5O_TAPS) return -1;
+    const int64_t Ho = (H - 4 + 1) / 2, Wo = (W - 4 + 1) / 2;
+    double K[SC5O_TAPS * SC5O_TAPS];
+    sc5o_outer(k, K);
+    for (int64_t p = 0; p < P; ++p) {
+        const double *Ap = A + p * H * W;
+        double *Bp = B + p * Ho * Wo;
+        for (int64_t y = 0; y < Ho; ++y)
+            for (int64_t x = 0; x < Wo; ++x) {
+                double s = 0.0;
+                for (int i = 0; i < SC5O_TAPS; ++i)
+                    for (int j = 0; j < SC5O_TAPS; ++j)
+                        s += Ap[(2 * y + i) * W + (2 * x + j)] * K[i * SC5O_TAPS + j];
+                Bp[y * Wo + x] = s;
+            }
+    }
+    return 0;
+}
+
 /* ---- storage-format decoders (exact, from the published bit layouts) ---- */
 
 /* bfloat16: the upper 16 bits of an IEEE binary32 (1 sign, 8 exponent, 7 fraction). */

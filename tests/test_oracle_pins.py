@@ -21,6 +21,10 @@ What each pin fixes:
                        followed by the vertical pass (Sec. 1, Sec. 5.1).
 * decoders          -- every bf16 / fp16 / fp8-e4m3 code against torch's and
                        numpy's own conversions, plus spot values of the formats.
+* REDUCE step       -- scipy's 2-D correlation kept at even rows and columns;
+                       the centre-tap delta picks A[2y+2][2x+2]; a ramp maps to
+                       the ramp at the even centres; output sizes for odd and
+                       even H-4, W-4.
 
 A last test plants plausible mistakes in copies of the C source and checks
 that at least one pin fails for each.
@@ -316,6 +320,36 @@ def pin_width_5_agrees_with_direct():
     assert np.max(np.abs(oracle.direct_n(A, k) - oracle.direct(A, k))) <= 1e-12 * 255
 
 
+def pin_reduce_scipy_subsampled():
+    from scipy.signal import correlate2d
+    for (H, W) in [(5, 5), (6, 7), (9, 13), (18, 21), (17, 32)]:
+        A = _rand_image(H * 7 + W, H, W, P=2)
+        k = _nonsym_k(H + W)
+        B = oracle.reduce2(A, k)
+        for p in range(2):
+            ref = correlate2d(A[p], np.outer(k, k), mode="valid")[::2, ::2]
+            assert B[p].shape == ref.shape
+            assert np.max(np.abs(B[p] - ref)) <= 1e-12 * 255
+
+
+def pin_reduce_delta_and_ramp():
+    A = _rand_image(77, 15, 20)
+    e2 = [0.0, 0.0, 1.0, 0.0, 0.0]
+    assert np.array_equal(oracle.reduce2(A, e2), A[:, 2:13:2, 2:18:2][:, :6, :8])
+    H, W = 16, 23
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    R = (0.75 * y - 1.25 * x + 3.0)[None]
+    k = np.array([1, 4, 6, 4, 1], np.float64) / 16
+    B = oracle.reduce2(R, k)
+    yo, xo = np.mgrid[0:B.shape[1], 0:B.shape[2]].astype(np.float64)
+    assert np.max(np.abs(B[0] - (0.75 * (2 * yo + 2) - 1.25 * (2 * xo + 2) + 3.0))) <= 1e-12 * 64
+
+
+def pin_reduce_sizes():
+    for (H, W, Ho, Wo) in [(5, 5, 1, 1), (6, 6, 1, 1), (7, 8, 2, 2), (8, 9, 2, 3), (100, 101, 48, 49)]:
+        assert oracle.reduce2(np.zeros((1, H, W)), [0, 0, 1, 0, 0]).shape == (1, Ho, Wo)
+
+
 PINS = [v for n, v in sorted(globals().items()) if n.startswith("pin_")]
 
 
@@ -335,13 +369,15 @@ def test_bad_sizes_rejected():
 
 # ---------------------------------------------------------------- mutants
 MUTANTS = {
-    "dropped kernel column": ("for (int j = 0; j < SC5O_TAPS; ++j)\n                        s +=",
-                              "for (int j = 0; j < SC5O_TAPS - 1; ++j)\n                        s +="),
+    "dropped kernel column": ("for (int j = 0; j < SC5O_TAPS; ++j)\n                        s += Ap[(y + i)",
+                              "for (int j = 0; j < SC5O_TAPS - 1; ++j)\n                        s += Ap[(y + i)"),
+    "reduce: dropped kernel column": ("for (int j = 0; j < SC5O_TAPS; ++j)\n                        s += Ap[(2 * y",
+                                      "for (int j = 0; j < SC5O_TAPS - 1; ++j)\n                        s += Ap[(2 * y"),
     "transposed image operand": ("Ap[(y + i) * W + (x + j)] * K[i * SC5O_TAPS + j]",
                                  "Ap[(y + j) * W + (x + i)] * K[i * SC5O_TAPS + j]"),
     "width-n transposed image operand": ("Ap[(y + i) * W + (x + j)] * K[i * n + j]",
                                          "Ap[(y + j) * W + (x + i)] * K[i * n + j]"),
-    "transposed K": ("* K[i * SC5O_TAPS + j];\n                Bp", "* K[j * SC5O_TAPS + i];\n                Bp"),
+    "transposed K": ("* K[i * SC5O_TAPS + j];\n                Bp[y * Wv", "* K[j * SC5O_TAPS + i];\n                Bp[y * Wv"),
     "flipped horizontal taps": ("W + x + t] * k[t]", "W + x + t] * k[4 - t]"),
     "flipped vertical taps": ("T[(p * H + y + t) * Wt + x] * k[t]", "T[(p * H + y + 4 - t) * Wt + x] * k[t]"),
     "outer product index": ("K[i * SC5O_TAPS + j] = k[i] * k[j]", "K[i * SC5O_TAPS + j] = k[i] * k[4 - j]"),
@@ -358,6 +394,9 @@ MUTANTS = {
     "width-n dropped row": ("for (int64_t i = 0; i < n; ++i)\n                    for (int64_t j = 0; j < n; ++j)",
                             "for (int64_t i = 1; i < n; ++i)\n                    for (int64_t j = 0; j < n; ++j)"),
     "width-n VALID size": ("const int64_t Hv = H - n + 1, Wv = W - n + 1;", "const int64_t Hv = H - n + 1, Wv = W - n;"),
+    "reduce: no column stride": ("Ap[(2 * y + i) * W + (2 * x + j)]", "Ap[(2 * y + i) * W + (x + j)]"),
+    "reduce: odd phase": ("Ap[(2 * y + i) * W + (2 * x + j)]", "Ap[(2 * y + 1 + i) * W + (2 * x + j)]"),
+    "reduce: output height rounded down": ("const int64_t Ho = (H - 4 + 1) / 2,", "const int64_t Ho = (H - 4) / 2,"),
 }
 
 
