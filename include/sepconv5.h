@@ -92,9 +92,19 @@ typedef enum {
 typedef enum {
     SC5_ALGO_FUSED = 0,     /* single pass, separable arithmetic (10 FMA per output) */
     SC5_ALGO_TWO_PASS = 1,  /* horizontal pass to an FP32 intermediate in HBM, then vertical pass */
-    SC5_ALGO_DIRECT = 2     /* single pass, direct form: 25 products per output with the 5x5
+    SC5_ALGO_DIRECT = 2,    /* single pass, direct form: 25 products per output with the 5x5
                                matrix K (Eq. 1 / Eq. 3); sepconv5_run uses K = k k^T rounded to
                                FP32, sepconv5_run_K takes any K */
+    SC5_ALGO_REDUCE = 3     /* one pyramid REDUCE step: the fused result kept at every second row
+                               and column.  The paper names convolution and scaling as the two
+                               costly steps of its stereo pipeline (Sec. 1) without defining the
+                               scaling; this is the blur-then-subsample reading.  Plane p of the
+                               output is Ho x Wo with Ho = ceil((H-4)/2), Wo = ceil((W-4)/2),
+                               rows out_pitch >= Wo apart, planes Ho*out_pitch apart; output
+                               (y, x) is the VALID output (2y, 2x), centred on input (2y+2, 2x+2),
+                               bit for bit the SC5_ALGO_FUSED value there.  Planar, width 5,
+                               SC5_BORDER_VALID, stacked planes (plane strides 0); every storage
+                               pair.  Such a plan runs through sepconv5_run only. */
 } sc5_algo;
 
 /* Image layouts.  SC5_LAYOUT_HWC: pixel-interleaved 3-plane images (RGB),

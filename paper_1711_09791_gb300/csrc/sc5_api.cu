@@ -352,6 +352,75 @@ static sc5_status run_hwc(sc5_plan p, const void *in, void *out, const float *k,
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "HWC launch");
 }
 
+// One pyramid REDUCE step: validation and plan.
+static sc5_status plan_reduce(const sc5_plan_desc &d, sc5_plan *out)
+{
+    if (d.taps != kTaps || d.border != SC5_BORDER_VALID)
+        return fail(SC5_EINVAL, "the REDUCE step is built for width 5 and SC5_BORDER_VALID");
+    if (!default_strides(d)) return fail(SC5_EINVAL, "the REDUCE step takes stacked planes (plane strides 0)");
+    FusedShape sh;
+    if (!reduce_shape(d.in_dtype, d.out_dtype, &sh))
+        return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built for the REDUCE step", d.in_dtype, d.out_dtype);
+    // the full-resolution VALID output is never stored; check the input side only
+    sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
+                                d.in_pitch, d.W - kHalo, 1.f, 1.f, false);
+    if (st != SC5_OK) return st;
+    const int64_t Wo = (d.W - kHalo + 1) / 2;
+    if (d.out_pitch < Wo) return fail(SC5_EINVAL, "REDUCE out_pitch %lld < Wo %lld", (long long)d.out_pitch,
+                                      (long long)Wo);
+    sc5_plan p = new (std::nothrow) sc5_plan_s;
+    if (!p) return fail(SC5_ENOMEM, "host allocation failed");
+    p->d = d;
+    cudaGetDevice(&p->device);
+    p->shape = sh;
+    p->ctas_per_sm = d.ctas_per_sm > 0 ? d.ctas_per_sm : 0;
+    if (cudaEventCreateWithFlags(&p->ws_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete p;
+        return fail(SC5_ECUDA, "cudaEventCreate failed");
+    }
+    *out = p;
+    return SC5_OK;
+}
+
+static bool is_reduce(const sc5_plan_desc &d) { return d.layout == SC5_LAYOUT_PLANAR && d.algo == SC5_ALGO_REDUCE; }
+
+static sc5_status run_reduce(sc5_plan p, const void *in, void *out, const float *k, float in_scale,
+                             float out_scale, cudaStream_t s)
+{
+    const sc5_plan_desc &d = p->d;
+    const int eo = dtype_bytes(d.out_dtype);
+    if (!in || !out) return fail(SC5_EINVAL, "null image pointer");
+    if (reinterpret_cast<uintptr_t>(in) % 16) return fail(SC5_EINVAL, "input must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out) % eo) return fail(SC5_EINVAL, "output not aligned to its element size");
+    if (!(in_scale > 0.f) || !std::isfinite(in_scale) || !(out_scale > 0.f) || !std::isfinite(out_scale))
+        return fail(SC5_EINVAL, "scales must be finite and > 0");
+    if (!taps_finite(k)) return fail(SC5_EINVAL, "taps must be finite");
+    const int Ho = (d.H - kHalo + 1) / 2, Wo = (d.W - kHalo + 1) / 2;
+    const int ei = dtype_bytes(d.in_dtype);
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    const char *a_end = a + (static_cast<size_t>(d.planes) * d.H * d.in_pitch) * ei;
+    const char *b_end = b + (static_cast<size_t>(d.planes - 1) * Ho * d.out_pitch +
+                             static_cast<size_t>(Ho - 1) * d.out_pitch + Wo) * eo;
+    if (a < b_end && b < a_end) return fail(SC5_EINVAL, "input and output overlap");
+    ImgDesc desc;
+    std::memset(&desc, 0, sizeof desc);
+    sc5_status st = encode_image_map(&desc.tmap, d.in_dtype, in, d.planes, d.H, d.W, d.in_pitch,
+                                     box_w_for(d.in_dtype, p->shape.tile_w, kTaps), p->shape.tile_h + kHalo);
+    if (st != SC5_OK) return st;
+    desc.out = out;
+    desc.out_pitch = d.out_pitch;
+    desc.out_plane = static_cast<int64_t>(Ho) * d.out_pitch;
+    desc.Hv = Ho;
+    desc.Wv = Wo;
+    desc.tiles_x = (Wo + p->shape.tile_w / 2 - 1) / (p->shape.tile_w / 2);
+    desc.tiles_y = (Ho + p->shape.tile_h / 2 - 1) / (p->shape.tile_h / 2);
+    for (int i = 0; i < kTaps; ++i) desc.k[i] = k[i];
+    desc.oscale = static_cast<float>(static_cast<double>(out_scale) / static_cast<double>(in_scale));
+    const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
+    cudaError_t e = launch_reduce(d.in_dtype, d.out_dtype, desc, ntiles, p->ctas_per_sm, s);
+    return e == cudaSuccess ? SC5_OK : fail_cuda(e, "REDUCE launch");
+}
+
 extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
 {
     clear_error();
@@ -361,6 +430,7 @@ extern "C" sc5_status sepconv5_plan(const sc5_plan_desc *desc, sc5_plan *out)
     if (d.taps == 0) d.taps = kTaps;
     if (d.layout == SC5_LAYOUT_HWC) return plan_hwc(d, out);
     if (d.layout != SC5_LAYOUT_PLANAR) return fail(SC5_EINVAL, "unknown layout %d", d.layout);
+    if (d.algo == SC5_ALGO_REDUCE) return plan_reduce(d, out);
     if (d.algo != SC5_ALGO_FUSED && d.algo != SC5_ALGO_TWO_PASS && d.algo != SC5_ALGO_DIRECT)
         return fail(SC5_EINVAL, "unknown algo %d", d.algo);
     if (d.taps != 3 && d.taps != 5 && d.taps != 7 && d.taps != 9)
@@ -491,6 +561,7 @@ extern "C" sc5_status sepconv5_run(sc5_plan p, const void *in, void *out, const 
     if (!p || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
     if (d.layout == SC5_LAYOUT_HWC) return run_hwc(p, in, out, k, in_scale, out_scale, static_cast<cudaStream_t>(stream));
+    if (is_reduce(d)) return run_reduce(p, in, out, k, in_scale, out_scale, static_cast<cudaStream_t>(stream));
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, in, out, d.planes, d.H, d.W, d.in_pitch,
                                 d.out_pitch, in_scale, out_scale, true, d.in_plane_stride, d.out_plane_stride,
                                 taps_of(d));
@@ -532,6 +603,7 @@ extern "C" sc5_status sepconv5_run_inplace(sc5_plan p, void *img, const float k[
     clear_error();
     if (!p || !img || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (is_reduce(d)) return fail(SC5_EINVAL, "a REDUCE plan runs through sepconv5_run only");
     if (d.in_dtype != d.out_dtype || d.border != SC5_BORDER_KEEP || d.out_pitch != d.in_pitch)
         return fail(SC5_EINVAL, "in-place needs in_dtype == out_dtype, border KEEP and out_pitch == in_pitch");
     if (!default_strides(d)) return fail(SC5_EINVAL, "in-place takes stacked planes (plane strides 0)");
@@ -577,6 +649,7 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
     clear_error();
     if (!p || !host_in || !host_out || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (is_reduce(d)) return fail(SC5_EINVAL, "a REDUCE plan runs through sepconv5_run only");
     if (!default_strides(d)) return fail(SC5_EINVAL, "the offload call takes stacked planes (plane strides 0)");
     if (taps_of(d) != kTaps || d.layout != SC5_LAYOUT_PLANAR)
         return fail(SC5_EINVAL, "the offload call is built for planar images of width 5");
@@ -671,6 +744,7 @@ extern "C" sc5_status sepconv5_hpass(sc5_plan p, const void *in, float *T, int64
     clear_error();
     if (!p || !in || !T || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (is_reduce(d)) return fail(SC5_EINVAL, "a REDUCE plan runs through sepconv5_run only");
     if (d.layout != SC5_LAYOUT_PLANAR || taps_of(d) != kTaps)
         return fail(SC5_EINVAL, "the separate passes take planar images of width 5");
     if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)
@@ -688,6 +762,7 @@ extern "C" sc5_status sepconv5_vpass(sc5_plan p, const float *T, int64_t t_pitch
     clear_error();
     if (!p || !out || !T || !k) return fail(SC5_EINVAL, "null argument");
     const sc5_plan_desc &d = p->d;
+    if (is_reduce(d)) return fail(SC5_EINVAL, "a REDUCE plan runs through sepconv5_run only");
     if (d.layout != SC5_LAYOUT_PLANAR || taps_of(d) != kTaps)
         return fail(SC5_EINVAL, "the separate passes take planar images of width 5");
     if (t_pitch < d.W - kHalo || t_pitch % 4 || reinterpret_cast<uintptr_t>(T) % 16)

@@ -17,7 +17,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16", "fp8e4m3"])
     ap.add_argument("--out", default=None, help="output format (default: the input format)")
-    ap.add_argument("--algo", default="fused", choices=["fused", "two_pass", "direct"])
+    ap.add_argument("--algo", default="fused", choices=["fused", "two_pass", "direct", "reduce"])
     ap.add_argument("--planes", type=int, default=3)
     ap.add_argument("--H", type=int, default=8192)
     ap.add_argument("--W", type=int, default=8192)
@@ -56,7 +56,9 @@ def main():
     else:
         A = torch.zeros((P, H, pitch), dtype=tdt[a.dtype], device="cuda")
         A[:, :, :W] = (x * scale).to(tdt[a.dtype])
-        out = torch.empty((P, H - 4, opitch), dtype=tdt[out_dtype], device="cuda")
+        Ho, Wo = (sc5.reduce_dims(H, W) if a.algo == "reduce" else (H - 4, W - 4))
+        opitch = -(-Wo * eo // 16) * 16 // eo if a.algo == "reduce" else opitch
+        out = torch.empty((P, Ho, opitch), dtype=tdt[out_dtype], device="cuda")
     del x
     plan = sc5.Plan(P, H, W, pitch, opitch, a.dtype, out_dtype, "valid", a.algo, th, tw, st, a.ctas,
                     layout=a.layout)
@@ -75,7 +77,8 @@ def main():
         times.append(e0.elapsed_time(e1))
     times.sort()
     ms = times[len(times) // 2]
-    alg = P * H * W * es + P * (H - 4) * (W - 4) * eo
+    Ho, Wo = (sc5.reduce_dims(H, W) if a.algo == "reduce" else (H - 4, W - 4))
+    alg = P * H * W * es + P * Ho * Wo * eo
     if sc5.device_status(stream) != 0:
         raise SystemExit("a kernel reported a device error")
     plan.close()

@@ -23,7 +23,7 @@ DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8e4m3": 3}
 DTYPE_BYTES = {"f32": 4, "bf16": 2, "f16": 2, "fp8e4m3": 1}
 BORDERS = {"valid": 0, "keep": 1}
 LAYOUTS = {"planar": 0, "hwc": 1}
-ALGOS = {"fused": 0, "two_pass": 1, "direct": 2}
+ALGOS = {"fused": 0, "two_pass": 1, "direct": 2, "reduce": 3}
 
 
 class Sepconv5Error(RuntimeError):
@@ -287,6 +287,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def reduce_dims(H: int, W: int) -> tuple[int, int]:
+    """Plane size (Ho, Wo) of one REDUCE step (algo="reduce") of an H x W plane."""
+    return (H - 3) // 2, (W - 3) // 2
 
 
 def device_status(stream=None) -> int:

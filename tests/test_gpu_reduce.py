@@ -1,0 +1,144 @@
+"""GPU parity of the pyramid REDUCE step (SC5_ALGO_REDUCE) through the C ABI.
+
+* Every storage pair on ragged sizes: bitwise equal to the fused result at
+  every second row and column, and within the format's bound of the FP64
+  oracle's REDUCE step on the decoded inputs.
+* A five-level FP32 pyramid: level L of the GPU chain against L oracle steps
+  applied to the original image (the oracle never sees a GPU result), within
+  L times the FP32 bound.
+* 3 x 8192 x 8192 FP32 at sampled outputs against Eq. 1 at (2y, 2x).
+* Plans and calls the step does not support are refused.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_09791_gb300 import synth
+from tests import _util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc5():
+    import torch  # noqa: F401
+    from paper_1711_09791_gb300 import sepconv5
+    sepconv5.load()
+    return sepconv5
+
+
+PAIRS = [("f32", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
+         ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
+SIZES = [(5, 5), (6, 7), (37, 131), (130, 261), (300, 517)]
+
+
+def _stored(x, dtype):
+    scale = synth.fp8_scale(x) if dtype == "fp8e4m3" else 1.0
+    codes = synth.to_storage(x, dtype, scale)
+    P, H, W = codes.shape
+    pitch = U.pitch_for(W, dtype)
+    padded = np.zeros((P, H, pitch), codes.dtype)
+    padded[:, :, :W] = codes
+    return padded, scale
+
+
+def _reduce(sc5, A_dev, H, W, pitch, k, in_dtype, out_dtype, in_scale, out_scale, P=3):
+    import torch
+    Ho, Wo = sc5.reduce_dims(H, W)
+    op = U.pitch_for(Wo, out_dtype)
+    out = U.empty_dev((P, Ho, op), out_dtype)
+    plan = sc5.Plan(P, H, W, pitch, op, in_dtype, out_dtype, algo="reduce")
+    plan.run(A_dev, out, k, in_scale, out_scale)
+    torch.cuda.synchronize()
+    assert sc5.device_status() == 0
+    plan.close()
+    res = U.from_dev(out, out_dtype)
+    assert U.sentinel_intact(res[:, :, Wo:], out_dtype), "wrote past Wo"
+    return res[:, :, :Wo], out
+
+
+def _fused(sc5, A_dev, H, W, pitch, k, in_dtype, out_dtype, in_scale, out_scale, P=3):
+    import torch
+    op = U.pitch_for(W - 4, out_dtype)
+    out = U.empty_dev((P, H - 4, op), out_dtype)
+    plan = sc5.Plan(P, H, W, pitch, op, in_dtype, out_dtype)
+    plan.run(A_dev, out, k, in_scale, out_scale)
+    torch.cuda.synchronize()
+    plan.close()
+    return U.from_dev(out, out_dtype)[:, :, :W - 4]
+
+
+@pytest.mark.parametrize("in_dtype,out_dtype", PAIRS)
+@pytest.mark.parametrize("H,W", SIZES)
+def test_reduce_equals_fused_at_even_positions_and_oracle(sc5, in_dtype, out_dtype, H, W):
+    x = synth.image(H * 31 + W, H, W)
+    padded, scale = _stored(x, in_dtype)
+    pitch = padded.shape[2]
+    k = synth.kernel_normalised(H + W)
+    out_scale = 1.0 if out_dtype == "f32" else scale
+    A_dev = U.to_dev(padded)
+    got, _ = _reduce(sc5, A_dev, H, W, pitch, k, in_dtype, out_dtype, scale, out_scale)
+    full = _fused(sc5, A_dev, H, W, pitch, k, in_dtype, out_dtype, scale, out_scale)
+    assert np.array_equal(got, full[:, ::2, ::2])
+    ref = oracle.reduce2(U.decode(padded[:, :, :W], in_dtype, scale), k)
+    dec = U.decode(got, out_dtype, out_scale)
+    assert dec.shape == ref.shape
+    if out_dtype == "f32":
+        assert U.max_abs(dec, ref) <= U.FP32_TOL
+    else:
+        assert np.all(np.abs(dec - ref) <= U.stored_tolerance(ref, out_dtype, out_scale, U.FP32_TOL))
+
+
+def test_five_level_pyramid(sc5):
+    import torch
+    H = W = 1030
+    pitch = U.pitch_for(W, "f32")
+    x = synth.image(17, H, W, pitch=pitch)  # NaN in the padding columns
+    k = synth.kernel_binomial()
+    cur = U.to_dev(x)
+    h, w = H, W
+    ref = x[:, :, :W].astype(np.float64)
+    for level in range(1, 6):
+        got, out = _reduce(sc5, cur, h, w, pitch, k, "f32", "f32", 1.0, 1.0)
+        ref = oracle.reduce2(ref, k)
+        assert got.shape == ref.shape
+        assert U.max_abs(got, ref) <= level * U.FP32_TOL, level
+        cur, pitch = out, out.shape[2]
+        h, w = got.shape[1], got.shape[2]
+    assert (h, w) == (29, 29)
+    torch.cuda.synchronize()
+
+
+def test_full_size_sampled(sc5):
+    import torch
+    P, H, W = 3, 8192, 8192
+    A = synth.image(2, H, W)
+    k = synth.kernel_normalised(2)
+    got, _ = _reduce(sc5, U.to_dev(A), H, W, W, k, "f32", "f32", 1.0, 1.0)
+    Ho, Wo = sc5.reduce_dims(H, W)
+    g = synth.rng(8)
+    pts = np.stack([g.integers(0, P, 4000), g.integers(0, Ho, 4000), g.integers(0, Wo, 4000)], axis=1)
+    corners = [(p, y, x) for p in range(P) for y in (0, Ho - 1) for x in (0, Wo - 1)]
+    pts = np.concatenate([pts, np.array(corners)])
+    full_pts = pts.copy()
+    full_pts[:, 1:] *= 2  # REDUCE output (y, x) is the VALID output (2y, 2x)
+    ref = oracle.points_f32(A, k, full_pts)
+    vals = got[pts[:, 0], pts[:, 1], pts[:, 2]].astype(np.float64)
+    assert np.max(np.abs(vals - ref)) <= U.FP32_TOL
+    torch.cuda.synchronize()
+
+
+def test_unsupported_reduce_plans_and_calls_refused(sc5):
+    import torch
+    with pytest.raises(sc5.Sepconv5Error) as e:
+        sc5.Plan(3, 64, 64, 64, 30, algo="reduce", border="keep")
+    assert e.value.status == sc5.EINVAL
+    with pytest.raises(sc5.Sepconv5Error):
+        sc5.Plan(3, 64, 64, 64, 29, algo="reduce")  # out_pitch < Wo = 30
+    plan = sc5.Plan(3, 64, 68, 68, 32, algo="reduce")
+    A = torch.zeros((3, 64, 68), dtype=torch.float32).pin_memory()
+    out = torch.zeros((3, 30, 32), dtype=torch.float32).pin_memory()
+    with pytest.raises(sc5.Sepconv5Error):
+        plan.run_host(A, out, [0, 0, 1, 0, 0])
+    assert plan.info()["tile_w"] == 128
+    plan.close()
