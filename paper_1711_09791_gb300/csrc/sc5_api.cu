@@ -359,8 +359,12 @@ static sc5_status plan_reduce(const sc5_plan_desc &d, sc5_plan *out)
         return fail(SC5_EINVAL, "the REDUCE step is built for width 5 and SC5_BORDER_VALID");
     if (!default_strides(d)) return fail(SC5_EINVAL, "the REDUCE step takes stacked planes (plane strides 0)");
     FusedShape sh;
-    if (!reduce_shape(d.in_dtype, d.out_dtype, &sh))
+    if (!reduce_shape(d.in_dtype, d.out_dtype, 0, 0, &sh))
         return fail(SC5_EINVAL, "dtype pair (%d -> %d) not built for the REDUCE step", d.in_dtype, d.out_dtype);
+    if ((d.tile_h || d.stages) && !reduce_shape(d.in_dtype, d.out_dtype, d.tile_h ? d.tile_h : sh.tile_h, d.stages, &sh))
+        return fail(SC5_EINVAL, "no compiled REDUCE shape with %d input rows per tile and %d stages", d.tile_h,
+                    d.stages);
+    if (d.tile_w && d.tile_w != sh.tile_w) return fail(SC5_EINVAL, "REDUCE tiles are %d input columns wide", sh.tile_w);
     // the full-resolution VALID output is never stored; check the input side only
     sc5_status st = check_image(d.in_dtype, d.out_dtype, d.border, nullptr, nullptr, d.planes, d.H, d.W,
                                 d.in_pitch, d.W - kHalo, 1.f, 1.f, false);
@@ -417,7 +421,7 @@ static sc5_status run_reduce(sc5_plan p, const void *in, void *out, const float 
     for (int i = 0; i < kTaps; ++i) desc.k[i] = k[i];
     desc.oscale = static_cast<float>(static_cast<double>(out_scale) / static_cast<double>(in_scale));
     const int64_t ntiles = static_cast<int64_t>(d.planes) * desc.tiles_x * desc.tiles_y;
-    cudaError_t e = launch_reduce(d.in_dtype, d.out_dtype, desc, ntiles, p->ctas_per_sm, s);
+    cudaError_t e = launch_reduce(d.in_dtype, d.out_dtype, p->shape, desc, ntiles, p->ctas_per_sm, s);
     return e == cudaSuccess ? SC5_OK : fail_cuda(e, "REDUCE launch");
 }
 

@@ -79,12 +79,13 @@ int hwc_tile_h(int in_dtype, int out_dtype); // output rows per tile (0: pair no
 size_t hwc_desc_size();
 void hwc_fill(void *desc, const CUtensorMap &m, void *out, int64_t out_pitch, int Hv, int Wv, int tile_h,
               const float *k, float oscale, bool vec);
-// Pyramid REDUCE kernel (sc5_reduce.cu): its tile shape for a dtype pair
-// (false: pair not built) and its launcher; desc.Hv / desc.Wv hold the output
-// extents and desc.tiles_x / desc.tiles_y the grid of TH x 128 input tiles.
-bool reduce_shape(int in_dtype, int out_dtype, FusedShape *sh);
-cudaError_t launch_reduce(int in_dtype, int out_dtype, const ImgDesc &desc, int64_t ntiles, int ctas_per_sm,
-                          cudaStream_t st);
+// Pyramid REDUCE kernel (sc5_reduce.cu): the compiled shape with tile_h input
+// rows per tile and `stages` stages (tile_h 0: the default; stages 0: any),
+// false if none; and its launcher.  desc.Hv / desc.Wv hold the output extents
+// and desc.tiles_x / desc.tiles_y the grid of TH x 128 input tiles.
+bool reduce_shape(int in_dtype, int out_dtype, int tile_h, int stages, FusedShape *sh);
+cudaError_t launch_reduce(int in_dtype, int out_dtype, const FusedShape &sh, const ImgDesc &desc, int64_t ntiles,
+                          int ctas_per_sm, cudaStream_t st);
 // ctas_per_sm <= 0 or above what fits: as many CTAs per SM as fit.
 cudaError_t launch_hwc(int in_dtype, int out_dtype, const void *desc, int64_t ntiles, int ctas_per_sm, cudaStream_t st);
 

@@ -182,46 +182,81 @@ ReduceEntry reduce_entry()
                        S * fused_stage_bytes<TIn, TH, kReduceTW, kReduceTaps>(), 32 * (TH / R + 1)};
 }
 
-bool reduce_lookup(int in_dtype, int out_dtype, ReduceEntry *e)
+// Compiled shapes per storage pair, (input rows per tile, input rows per warp,
+// stages), unique per (input rows per tile, stages).  A warp re-forms the row
+// pass of the R+3 input rows its R/2 output rows need, so taller strips repeat
+// less of it ((R+3)/R: 1.75 at R = 4, 1.19 at R = 16).  The first entry is the
+// default, chosen by measurement on 3x8192x8192: FP32 128/8/3 (0.156 ms
+// against 0.160 ms for 64/4/3); 16-bit to 16-bit 128/16/3 (BF16 0.086 ms
+// against 0.126 ms); 16-bit to FP32 128/8/4 (BF16 0.099 ms); FP8 to FP8 and
+// to FP32 128/16/5 (0.095 / 0.096 ms against 0.142 / 0.107 ms).
+#define SC5_RED(TI, TO, TH, R, S) reduce_entry<TI, TO, TH, R, S>()
+constexpr int kReduceShapes = 4;
+
+const ReduceEntry *reduce_entries(int in_dtype, int out_dtype)
 {
-    // (input rows per tile, input rows per warp, stages): 16 consumer warps
-    static const ReduceEntry f32_f32 = reduce_entry<float, float, 64, 4, 3>();
-    static const ReduceEntry bf_bf = reduce_entry<bf16_t, bf16_t, 64, 4, 4>();
-    static const ReduceEntry bf_f32 = reduce_entry<bf16_t, float, 64, 4, 4>();
-    static const ReduceEntry h_h = reduce_entry<f16_t, f16_t, 64, 4, 4>();
-    static const ReduceEntry h_f32 = reduce_entry<f16_t, float, 64, 4, 4>();
-    static const ReduceEntry e_e = reduce_entry<fp8e4m3_t, fp8e4m3_t, 64, 4, 6>();
-    static const ReduceEntry e_f32 = reduce_entry<fp8e4m3_t, float, 64, 4, 6>();
-    const ReduceEntry *r = nullptr;
-    if (in_dtype == SC5_F32 && out_dtype == SC5_F32) r = &f32_f32;
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) r = &bf_bf;
-    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) r = &bf_f32;
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) r = &h_h;
-    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) r = &h_f32;
-    if (in_dtype == SC5_FP8E4M3 && out_dtype == SC5_FP8E4M3) r = &e_e;
-    if (in_dtype == SC5_FP8E4M3 && out_dtype == SC5_F32) r = &e_f32;
-    if (!r) return false;
-    *e = *r;
-    return true;
+    static const ReduceEntry f32_f32[] = {SC5_RED(float, float, 128, 8, 3), SC5_RED(float, float, 64, 4, 3),
+                                          SC5_RED(float, float, 64, 8, 2), SC5_RED(float, float, 128, 16, 2)};
+#define SC5_RED_16(TI)                                                                               \
+    {SC5_RED(TI, TI, 128, 16, 3), SC5_RED(TI, TI, 64, 4, 4), SC5_RED(TI, TI, 64, 8, 3),             \
+     SC5_RED(TI, TI, 128, 8, 4)}
+#define SC5_RED_16_F32(TI)                                                                           \
+    {SC5_RED(TI, float, 128, 8, 4), SC5_RED(TI, float, 64, 4, 4), SC5_RED(TI, float, 64, 8, 3),     \
+     SC5_RED(TI, float, 128, 16, 3)}
+    static const ReduceEntry bf_bf[] = SC5_RED_16(bf16_t);
+    static const ReduceEntry bf_f32[] = SC5_RED_16_F32(bf16_t);
+    static const ReduceEntry h_h[] = SC5_RED_16(f16_t);
+    static const ReduceEntry h_f32[] = SC5_RED_16_F32(f16_t);
+    static const ReduceEntry e_e[] = {SC5_RED(fp8e4m3_t, fp8e4m3_t, 128, 16, 5),
+                                      SC5_RED(fp8e4m3_t, fp8e4m3_t, 64, 4, 6),
+                                      SC5_RED(fp8e4m3_t, fp8e4m3_t, 64, 8, 5),
+                                      SC5_RED(fp8e4m3_t, fp8e4m3_t, 128, 8, 6)};
+    static const ReduceEntry e_f32[] = {SC5_RED(fp8e4m3_t, float, 128, 16, 5), SC5_RED(fp8e4m3_t, float, 64, 4, 6),
+                                        SC5_RED(fp8e4m3_t, float, 64, 8, 5), SC5_RED(fp8e4m3_t, float, 128, 8, 6)};
+#undef SC5_RED_16
+#undef SC5_RED_16_F32
+    if (in_dtype == SC5_F32 && out_dtype == SC5_F32) return f32_f32;
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_BF16) return bf_bf;
+    if (in_dtype == SC5_BF16 && out_dtype == SC5_F32) return bf_f32;
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F16) return h_h;
+    if (in_dtype == SC5_F16 && out_dtype == SC5_F32) return h_f32;
+    if (in_dtype == SC5_FP8E4M3 && out_dtype == SC5_FP8E4M3) return e_e;
+    if (in_dtype == SC5_FP8E4M3 && out_dtype == SC5_F32) return e_f32;
+    return nullptr;
+}
+
+// The entry with these input rows per tile and stages (0 = any stages), or
+// the default when tile_h is 0; false if none is compiled.
+bool reduce_lookup(int in_dtype, int out_dtype, int tile_h, int stages, ReduceEntry *e)
+{
+    const ReduceEntry *list = reduce_entries(in_dtype, out_dtype);
+    if (!list) return false;
+    for (int i = 0; i < kReduceShapes; ++i)
+        if (tile_h == 0 || (list[i].tile_h == tile_h && (stages == 0 || list[i].stages == stages))) {
+            *e = list[i];
+            return true;
+        }
+    return false;
 }
 
 }  // namespace
 
 int *status_word();  // sc5_fused.cu
 
-bool reduce_shape(int in_dtype, int out_dtype, FusedShape *sh)
+bool reduce_shape(int in_dtype, int out_dtype, int tile_h, int stages, FusedShape *sh)
 {
     ReduceEntry e;
-    if (!reduce_lookup(in_dtype, out_dtype, &e)) return false;
+    if (!reduce_lookup(in_dtype, out_dtype, tile_h, stages, &e)) return false;
     *sh = FusedShape{e.tile_h, kReduceTW, e.rows, e.stages};
     return true;
 }
 
-cudaError_t launch_reduce(int in_dtype, int out_dtype, const ImgDesc &desc, int64_t ntiles, int ctas_per_sm,
-                          cudaStream_t st)
+cudaError_t launch_reduce(int in_dtype, int out_dtype, const FusedShape &sh, const ImgDesc &desc, int64_t ntiles,
+                          int ctas_per_sm, cudaStream_t st)
 {
     ReduceEntry e;
-    if (!reduce_lookup(in_dtype, out_dtype, &e)) return cudaErrorInvalidValue;
+    if (!reduce_lookup(in_dtype, out_dtype, sh.tile_h, sh.stages, &e) || e.rows != sh.rows_per_thread)
+        return cudaErrorInvalidValue;
     if (ntiles <= 0) return cudaSuccess;
     static std::mutex mu;
     static std::set<std::pair<const void *, int>> done;

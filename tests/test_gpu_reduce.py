@@ -89,6 +89,40 @@ def test_reduce_equals_fused_at_even_positions_and_oracle(sc5, in_dtype, out_dty
         assert np.all(np.abs(dec - ref) <= U.stored_tolerance(ref, out_dtype, out_scale, U.FP32_TOL))
 
 
+@pytest.mark.parametrize("in_dtype,out_dtype", PAIRS)
+def test_every_compiled_reduce_shape(sc5, in_dtype, out_dtype):
+    """Each (input rows per tile, stages) a plan accepts runs the same
+    arithmetic: bitwise the fused result at even rows and columns."""
+    import torch
+    H, W = 300, 517
+    padded, scale = _stored(synth.image(5, H, W), in_dtype)
+    pitch = padded.shape[2]
+    k = synth.kernel_normalised(5)
+    out_scale = 1.0 if out_dtype == "f32" else scale
+    A_dev = U.to_dev(padded)
+    full = _fused(sc5, A_dev, H, W, pitch, k, in_dtype, out_dtype, scale, out_scale)[:, ::2, ::2]
+    Ho, Wo = sc5.reduce_dims(H, W)
+    op = U.pitch_for(Wo, out_dtype)
+    seen = set()
+    for th in (32, 64, 96, 128, 256):
+        for st in range(1, 9):
+            try:
+                plan = sc5.Plan(3, H, W, pitch, op, in_dtype, out_dtype, algo="reduce", tile_h=th, stages=st)
+            except sc5.Sepconv5Error as e:
+                assert e.status == sc5.EINVAL
+                continue
+            info = plan.info()
+            assert (info["tile_h"], info["stages"]) == (th, st)
+            out = U.empty_dev((3, Ho, op), out_dtype)
+            plan.run(A_dev, out, k, scale, out_scale)
+            torch.cuda.synchronize()
+            assert sc5.device_status() == 0
+            plan.close()
+            assert np.array_equal(U.from_dev(out, out_dtype)[:, :, :Wo], full), (th, st)
+            seen.add((th, st))
+    assert len(seen) == 4, seen
+
+
 def test_five_level_pyramid(sc5):
     import torch
     H = W = 1030
