@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed fused leg")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests per offered load")
-    ap.add_argument("--legs", default="c1,c3,c4,paper,c5", help="extra configs to run beside the headline")
+    ap.add_argument("--legs", default="c1,c3,c4,paper,pyramid,c5", help="extra configs to run beside the headline")
     return ap.parse_args()
 
 
@@ -313,6 +313,45 @@ def leg_paper_sizes(sc5, stream):
         del A, out
     torch.cuda.empty_cache()
     return res
+
+
+def leg_pyramid(sc5, synth, stream, A_dev, k):
+    """A five-level pyramid of the 3 x 8192 x 8192 FP32 image: five chained
+    REDUCE steps (blur with k, keep every second row and column), each level
+    the input of the next.  Per level: CUDA-event time and algorithmic bytes
+    (its input read once, its output written once)."""
+    import torch
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    levels, plans, bufs = [], [], []
+    cur, h, w, pitch = A_dev, H, W, W
+    for _ in range(5):
+        ho, wo = sc5.reduce_dims(h, w)
+        op = -(-wo // 4) * 4
+        out = torch.empty((P, ho, op), dtype=torch.float32, device=A_dev.device)
+        plans.append((sc5.Plan(P, h, w, pitch, op, algo="reduce"), cur, out))
+        levels.append({"in": [h, w], "out": [ho, wo], "bytes": P * h * w * 4 + P * ho * wo * 4})
+        bufs.append(out)
+        cur, h, w, pitch = out, ho, wo, op
+
+    def run_all():
+        for plan, src, dst in plans:
+            plan.run(src, dst, k, stream=stream)
+
+    total_ms = cuda_time(run_all, 50, 5, stream)
+    for lv, (plan, src, dst) in zip(levels, plans):
+        ms = cuda_time(lambda: plan.run(src, dst, k, stream=stream), 50, 5, stream)
+        lv["ms"] = round(ms, 5)
+        lv["frac_of_measured_hbm"] = round(lv["bytes"] / ms / 1e6 / peak, 4)
+    for plan, _, _ in plans:
+        plan.close()
+    if sc5.device_status(stream) != 0:
+        raise RuntimeError("a kernel reported a device error in the pyramid leg")
+    alg = sum(lv["bytes"] for lv in levels)
+    return {"workload": "5-level pyramid of 3x8192x8192 f32 (REDUCE steps), k as the headline",
+            "total_ms": round(total_ms, 5), "launches": len(levels),
+            "achieved_gbs": round(alg / total_ms / 1e6, 1), "frac_of_measured_hbm": round(alg / total_ms / 1e6 / peak, 4),
+            "levels": levels}
 
 
 def _batch_images(sc5, synth, dtype, shapes, x_dev, scales):
@@ -670,6 +709,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     plan.close()
     del A_host, out_host
     legs = [] if args.no_extras or rank != 0 else [x.strip() for x in args.legs.split(",") if x.strip()]
+    if "pyramid" in legs:
+        extras["pyramid"] = leg_pyramid(sepconv5, synth, stream, A_dev, k)
     if legs:
         import oracle
         del A_dev, out
