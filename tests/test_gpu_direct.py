@@ -50,7 +50,7 @@ def test_general_K_against_oracle(sc5, H, W):
     K = _general_K(H + W)
     ref = oracle.direct_K(A[:, :, :W].astype(np.float64), K.astype(np.float64))
     A_dev = U.to_dev(A)
-    for (th, tw, st) in [(0, 0, 0), (32, 128, 4)]:
+    for (th, tw, st) in [(0, 0, 0), (64, 128, 3), (32, 128, 4)]:
         got = _run(sc5, A_dev, 3, H, W, pitch, K=K, tile_h=th, tile_w=tw, stages=st)
         assert U.max_abs(got, ref) <= U.FP32_TOL, (th, tw, st)
 
