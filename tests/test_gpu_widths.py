@@ -49,6 +49,29 @@ def test_widths_against_oracle(sc5, n):
         assert U.max_abs(got, ref) <= U.FP32_TOL, (n, H, W)
 
 
+def test_width9_compiled_shapes_agree(sc5):
+    """Width 9 has two compiled shapes (2 and 3 stages): same bits, within the bound."""
+    import torch
+    H, W, n = 300, 517, 9
+    pitch = U.pitch_for(W, "f32")
+    A = synth.image(99, H, W, pitch=pitch)
+    k = _k(n, 99)
+    ref = oracle.direct_n(A[:, :, :W].astype(np.float64), k.astype(np.float64))
+    A_dev = U.to_dev(A)
+    op = U.pitch_for(W - n + 1, "f32")
+    res = []
+    for st in (3, 2):
+        out = U.empty_dev((3, H - n + 1, op), "f32")
+        plan = sc5.Plan(3, H, W, pitch, op, "f32", "f32", "valid", "fused", 128, 128, st, taps=n)
+        plan.run(A_dev, out, k)
+        torch.cuda.synchronize()
+        assert sc5.device_status() == 0
+        plan.close()
+        res.append(U.from_dev(out, "f32")[:, :, :W - n + 1])
+    assert np.array_equal(res[0], res[1])
+    assert U.max_abs(res[0], ref) <= U.FP32_TOL
+
+
 @pytest.mark.parametrize("n", [3, 7, 9])
 def test_width_deltas_exact_and_keep_frame(sc5, n):
     H, W = 40, 136
