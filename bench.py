@@ -741,9 +741,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "metric": METRIC, "value": round(value, 1), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid",
-                   "l2": "inputs larger than L2 (805 MB in, 804 MB out per step); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": run_config(world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
                      "peak_source": peak_src, "kernel": "fused_kernel<float,float> (single image)",
@@ -755,6 +753,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     line.update(extras)
     return line
+
+
+def run_config(world: int) -> dict:
+    """The workload both arms report (the reference arm times the oracle on it)."""
+    return {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid",
+            "l2": "inputs larger than L2 (805 MB in, 804 MB out per step); no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -780,7 +785,7 @@ def run_reference(args, rank: int, world: int):
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world,
             "steps": steps, "warmup": 3, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid"},
+            "config": run_config(world),
             "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
