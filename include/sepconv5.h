@@ -147,7 +147,10 @@ typedef struct {
     int32_t ctas_per_sm;           /* persistent CTAs per SM, capped at what fits; 0 =
                                       the planner's choice: the tuning table's entry,
                                       else the shape's measured default, else as many
-                                      as fit (HWC: as many as fit) */
+                                      as fit (HWC: as many as fit).  -1: as 0, except
+                                      that sepconv5_batch_create times every feasible
+                                      count on the batch itself and keeps the fastest
+                                      (those launches write the batch's outputs) */
     int64_t in_plane_stride, out_plane_stride;
     int32_t taps;                  /* kernel width: 0 or 5 (the paper's), or 3, 7, 9 */
     int32_t layout;                /* sc5_layout */

@@ -270,10 +270,10 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         if (i < 0) return fail(SC5_EINVAL, "no compiled fused shape %dx%d with %d stages for this dtype pair",
                                ov->tile_h, ov->tile_w, ov->stages);
         *idx = i;
-        *ctas = ov->ctas_per_sm;
+        *ctas = ov->ctas_per_sm > 0 ? ov->ctas_per_sm : 0;
     } else if (direct || taps != kTaps) {
         *idx = 0;
-        *ctas = (ov && ov->ctas_per_sm) ? ov->ctas_per_sm : fused_default_ctas(in_dtype, out_dtype, 0, direct, taps);
+        *ctas = (ov && ov->ctas_per_sm > 0) ? ov->ctas_per_sm : fused_default_ctas(in_dtype, out_dtype, 0, direct, taps);
     } else {
         int th, tw, stg, c;
         // the table's entry, else the shape's own default (0: as many as fit);
@@ -287,7 +287,7 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         }
         if (*idx < 0) *idx = 0;
         if (!tuned) *ctas = fused_default_ctas(in_dtype, out_dtype, *idx);
-        if (ov && ov->ctas_per_sm) *ctas = ov->ctas_per_sm;
+        if (ov && ov->ctas_per_sm > 0) *ctas = ov->ctas_per_sm;
     }
     const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, *idx, direct, taps);
     if (maxc <= 0) return fail(SC5_ECUDA, "occupancy query failed for fused shape %d", *idx);
@@ -859,7 +859,7 @@ sc5_status batch_shape(sc5_plan p, int n, const sc5_image *imgs, int *idx, int *
         return SC5_OK;
     }
     sc5_status st = choose_batch_shape(d.in_dtype, d.out_dtype, n, imgs, idx, ctas);
-    if (st == SC5_OK && d.ctas_per_sm) *ctas = std::min(*ctas, d.ctas_per_sm);
+    if (st == SC5_OK && d.ctas_per_sm > 0) *ctas = std::min(*ctas, d.ctas_per_sm);
     return st;
 }
 
@@ -939,6 +939,47 @@ struct sc5_batch_s {
     cudaGraphExec_t exec = nullptr;
 };
 
+// CTAs per SM for a batch, measured on the batch itself: every feasible count,
+// one warm-up and three timed launches each on a private stream, median kept
+// (the launches write the batch's outputs, as its first replay would).
+static cudaError_t time_batch_ctas(int in_dtype, int out_dtype, int idx, unsigned char *ws, size_t toff,
+                                   int64_t ntiles, int *ctas)
+{
+    const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, idx);
+    if (maxc < 1) return cudaErrorInvalidConfiguration;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, z = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&z);
+    float best = 0.f;
+    for (int c = 1; c <= maxc && e == cudaSuccess; ++c) {
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min(ntiles, static_cast<int64_t>(num_sms()) * c)));
+        std::vector<float> ts;
+        for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(a, s);
+            if (e == cudaSuccess)
+                e = launch_fused_batch(in_dtype, out_dtype, idx, reinterpret_cast<const ImgDesc *>(ws),
+                                       reinterpret_cast<const TileRec *>(ws + toff), ntiles, grid, s);
+            if (e == cudaSuccess) e = cudaEventRecord(z, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(z);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+            if (r > 0) ts.push_back(ms);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(ts.begin(), ts.end());
+        if (c == 1 || ts[1] < best) {
+            best = ts[1];
+            *ctas = c;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (z) cudaEventDestroy(z);
+    if (s) cudaStreamDestroy(s);
+    return e;
+}
+
 extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_image *imgs, sc5_batch *out)
 {
     clear_error();
@@ -964,6 +1005,8 @@ extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_ima
     cudaError_t e = cudaMalloc(&b->ws, blob.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->ws, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = fused_prepare(p->d.in_dtype, p->d.out_dtype, idx);
+    if (e == cudaSuccess && p->d.ctas_per_sm < 0)
+        e = time_batch_ctas(p->d.in_dtype, p->d.out_dtype, idx, b->ws, toff, b->ntiles, &ctas);
     const int64_t cap = static_cast<int64_t>(num_sms()) * ctas;
     b->grid = static_cast<int>(std::max<int64_t>(1, std::min(b->ntiles, cap)));
     cudaStream_t cs = nullptr;

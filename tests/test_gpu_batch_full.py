@@ -60,3 +60,40 @@ def test_full_batch_sampled(dtype):
         assert not torch.isnan(im["out"][:, :, :w - 4].float()).any()
     b.close()
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batch_ctas_timed_on_create(dtype):
+    """ctas_per_sm = -1: the batch times every feasible CTA count on itself at
+    creation; the outputs do not depend on the count (bitwise equal to an
+    explicit one CTA per SM) and the grid is a whole number of CTAs per SM."""
+    import torch
+    from paper_1711_09791_gb300 import sepconv5 as sc5
+    sc5.load()
+    shapes = synth.batch_shapes(5, 40)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
+    es = sc5.DTYPE_BYTES[dtype]
+    runs = []
+    for ctas in (1, -1):
+        imgs = []
+        for i, (h, w) in enumerate(shapes):
+            x = torch.from_numpy(synth.image(5000 + i, h, w)).cuda()
+            pitch = -(-w * es // 16) * 16 // es
+            A = torch.zeros((3, h, pitch), dtype=tdt, device="cuda")
+            A[:, :, :w] = x.to(tdt)
+            op = -(-(w - 4) // 4) * 4
+            imgs.append({"in": A, "out": torch.zeros((3, h - 4, op), dtype=tdt, device="cuda"), "H": h, "W": w,
+                         "in_pitch": pitch, "out_pitch": op, "k": synth.kernel_normalised(5000 + i)})
+        plan = sc5.Plan(3, 64, 64, in_dtype=dtype, ctas_per_sm=ctas)
+        b = sc5.Batch(plan, imgs)
+        b.launch()
+        torch.cuda.synchronize()
+        assert sc5.device_status() == 0
+        info = b.info()
+        n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert info["ctas"] % n_sms == 0 or info["ctas"] == info["tiles"]
+        runs.append([im["out"].clone() for im in imgs])
+        b.close()
+        plan.close()
+    for a, c in zip(*runs):
+        assert torch.equal(a, c)
