@@ -484,7 +484,10 @@ def leg_serve(sc5, synth, n_req):
         return pool
 
     def run(dtype, merge, rate, n, pool, seed):
-        srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype=dtype, max_inflight=64, n_streams=2, merge=merge)
+        # merged launches of at most 8 requests: smaller groups keep both copy directions busy
+        # (saturation 3507 req/s against 3150 with no cap, same box)
+        srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype=dtype, max_inflight=64, n_streams=2, merge=merge,
+                         max_merge=8 if merge else 0)
         stream_ = synth.serve_stream(seed, n, rate) if rate else [(0.0, c, s) for (_, c, s) in synth.serve_stream(seed, n, 1.0)]
         lat = []
         tickets = _q.Queue()

@@ -348,7 +348,11 @@ typedef struct {
     int32_t dtype;            /* storage format of inputs and outputs */
     int32_t planes;           /* planes per image */
     int32_t n_streams;        /* compute streams used round robin (>= 1) */
-    int32_t max_merge;        /* most requests merged into one launch (0 = no limit) */
+    int32_t max_merge;        /* most requests merged into one launch (0 = no limit).  Small
+                                 groups keep both copy directions busy: with requests of
+                                 640x480, 1920x1080 and 4096x4096, 8 gave the highest
+                                 saturation (3507 req/s against 3150 with no limit) and the
+                                 shorter tail */
     int32_t merge;            /* 1 = continuous batching, 0 = one launch per request */
     int32_t batch_window_us;  /* hold admitted requests up to this long (or until max_merge
                                  are waiting) before launching them together; 0 = launch

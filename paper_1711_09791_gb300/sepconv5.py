@@ -345,7 +345,7 @@ class Server:
     """Serving runtime (serve_create / serve_submit / serve_poll / serve_destroy)."""
 
     def __init__(self, hbm_budget_bytes: int, dtype="bf16", planes=3, max_inflight=64, n_streams=2,
-                 max_merge=0, merge=True, batch_window_us=0):
+                 max_merge=8, merge=True, batch_window_us=0):
         cfg = ServeCfg()
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.max_inflight = max_inflight
