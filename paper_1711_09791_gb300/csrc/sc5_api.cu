@@ -688,12 +688,16 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
         return e == cudaSuccess ? SC5_OK : fail_cuda(e, "copy to host");
     }
 
-    // bands of R output rows (a multiple of the tile height, about 8 per plane)
+    // Output bands of R rows (a multiple of the tile height, about 8 per plane).
+    // The image's first and last band are split into bands of about R/4 rows, so
+    // that the first kernel waits for a small copy and the last copy back is
+    // small.  Each band's input rows are copied just ahead of it: only the rows
+    // (band rows plus the 4-row halo) not yet on the device.
     const int th = p->shape.tile_h;
     const int R = std::max(th, (((Hv + 7) / 8) + th - 1) / th * th);
-    const int nb = (Hv + R - 1) / R;           // output bands per plane
-    const int nc = (d.H + R - 1) / R;          // input chunks per plane
-    const size_t need_ev = static_cast<size_t>(d.planes) * (nc + nb);
+    const int Rs = std::max(th, ((R + 3) / 4 + th - 1) / th * th);
+    const int nb = (Hv + R - 1) / R;
+    const size_t need_ev = static_cast<size_t>(d.planes) * 2 * (nb + 2 * ((R + Rs - 1) / Rs));
     while (p->ev.size() < need_ev) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -702,24 +706,29 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
     }
     size_t evi = 0;
     const int64_t cap = static_cast<int64_t>(num_sms()) * p->ctas_per_sm;
+    std::vector<std::pair<int, int>> bands;  // output rows [first, second) of one plane
     for (int pl = 0; pl < d.planes; ++pl) {
-        const size_t in_plane = in_row * d.H * pl, out_plane = out_row * Hv * pl;
-        int next_chunk = 0;
-        std::vector<cudaEvent_t> chunk_ev(nc);
+        bands.clear();
         for (int b = 0; b < nb; ++b) {
-            const int need = std::min(nc - 1, b + 1);
-            while (next_chunk <= need) {
-                const int r0 = next_chunk * R, rows = std::min(d.H - r0, R);
-                const size_t off = in_plane + in_row * r0;
-                e = cudaMemcpyAsync(din + off, hin + off, in_row * rows, cudaMemcpyHostToDevice, p->s_in);
+            const int y0 = b * R, y1 = std::min(Hv, y0 + R);
+            const bool split = (pl == 0 && b == 0) || (pl == d.planes - 1 && b == nb - 1);
+            for (int y = y0; y < y1; y += split ? Rs : R) bands.emplace_back(y, std::min(y1, y + (split ? Rs : R)));
+        }
+        const size_t in_plane = in_row * d.H * pl, out_plane = out_row * Hv * pl;
+        int loaded = 0;  // input rows of this plane already copied
+        cudaEvent_t in_ev = nullptr;
+        for (const auto &band : bands) {
+            const int y0 = band.first, rows_out = band.second - band.first;
+            const int need = std::min(d.H, band.second + kHalo);
+            if (need > loaded) {
+                const size_t off = in_plane + in_row * loaded;
+                e = cudaMemcpyAsync(din + off, hin + off, in_row * (need - loaded), cudaMemcpyHostToDevice, p->s_in);
                 if (e != cudaSuccess) return fail_cuda(e, "band copy to device");
-                chunk_ev[next_chunk] = p->ev[evi++];
-                cudaEventRecord(chunk_ev[next_chunk], p->s_in);
-                ++next_chunk;
+                in_ev = p->ev[evi++];
+                cudaEventRecord(in_ev, p->s_in);
+                loaded = need;
             }
-            cudaStreamWaitEvent(s, chunk_ev[need], 0);
-            const int y0 = b * R;
-            const int rows_out = std::min(Hv - y0, R);
+            cudaStreamWaitEvent(s, in_ev, 0);
             ImgDesc desc;
             st = fill_desc(&desc, d.in_dtype, d.out_dtype, d.border, p->shape, din + in_plane + in_row * y0,
                            dout + out_plane + out_row * y0, 1, rows_out + kHalo, d.W, d.in_pitch, d.out_pitch, k,
