@@ -317,39 +317,34 @@ def leg_paper_sizes(sc5, stream):
 
 
 def leg_pyramid(sc5, synth, stream, A_dev, k):
-    """A five-level pyramid of the 3 x 8192 x 8192 FP32 image: five chained
-    REDUCE steps (blur with k, keep every second row and column), each level
-    the input of the next.  Per level: CUDA-event time and algorithmic bytes
-    (its input read once, its output written once)."""
+    """A five-level pyramid of the 3 x 8192 x 8192 FP32 image through
+    sepconv5_pyramid_run: five chained REDUCE steps (blur with k, keep every
+    second row and column), each level the input of the next.  Whole-pyramid
+    CUDA-event time, and per level its REDUCE plan's time alone; algorithmic
+    bytes per level = its input read once plus its output written once."""
     import torch
     peaks = measured_peaks()
     peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
-    levels, plans, bufs = [], [], []
-    cur, h, w, pitch = A_dev, H, W, W
-    for _ in range(5):
-        ho, wo = sc5.reduce_dims(h, w)
-        op = -(-wo // 4) * 4
-        out = torch.empty((P, ho, op), dtype=torch.float32, device=A_dev.device)
-        plans.append((sc5.Plan(P, h, w, pitch, op, algo="reduce"), cur, out))
+    pyr = sc5.Pyramid(P, H, W, W, "f32", levels=5)
+    levels, bufs = [], []
+    for lv in range(1, 6):
+        (h, w, _), (ho, wo, op) = pyr.level(lv - 1), pyr.level(lv)
+        bufs.append(torch.empty((P, ho, op), dtype=torch.float32, device=A_dev.device))
         levels.append({"in": [h, w], "out": [ho, wo], "bytes": P * h * w * 4 + P * ho * wo * 4})
-        bufs.append(out)
-        cur, h, w, pitch = out, ho, wo, op
-
-    def run_all():
-        for plan, src, dst in plans:
-            plan.run(src, dst, k, stream=stream)
-
-    total_ms = cuda_time(run_all, 50, 5, stream)
-    for lv, (plan, src, dst) in zip(levels, plans):
+    total_ms = cuda_time(lambda: pyr.run(A_dev, bufs, k, stream=stream), 50, 5, stream)
+    srcs = [A_dev] + bufs[:-1]
+    for lv, src, dst in zip(levels, srcs, bufs):
+        h, w = lv["in"]
+        plan = sc5.Plan(P, h, w, src.shape[-1], dst.shape[-1], algo="reduce")
         ms = cuda_time(lambda: plan.run(src, dst, k, stream=stream), 50, 5, stream)
+        plan.close()
         lv["ms"] = round(ms, 5)
         lv["frac_of_measured_hbm"] = round(lv["bytes"] / ms / 1e6 / peak, 4)
-    for plan, _, _ in plans:
-        plan.close()
+    pyr.close()
     if sc5.device_status(stream) != 0:
         raise RuntimeError("a kernel reported a device error in the pyramid leg")
     alg = sum(lv["bytes"] for lv in levels)
-    return {"workload": "5-level pyramid of 3x8192x8192 f32 (REDUCE steps), k as the headline",
+    return {"workload": "5-level pyramid of 3x8192x8192 f32 (REDUCE steps, sepconv5_pyramid_run), k as the headline",
             "total_ms": round(total_ms, 5), "launches": len(levels),
             "achieved_gbs": round(alg / total_ms / 1e6, 1), "frac_of_measured_hbm": round(alg / total_ms / 1e6 / peak, 4),
             "levels": levels}

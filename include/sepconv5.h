@@ -282,6 +282,38 @@ SC5_API sc5_status sepconv5_two_pass_noalloc(const void *in, void *out, int32_t 
  * time). */
 SC5_API sc5_status sepconv5_device_status(void *stream, int32_t *code);
 
+/* ---------------------------------------------------------------- pyramids */
+
+/* A multi-scale pyramid: `levels` chained REDUCE steps (SC5_ALGO_REDUCE) of a
+ * planar image.  Level 0 is the input ([planes][H][in_pitch], in_dtype);
+ * level l >= 1 is the REDUCE step of level l-1, stored in out_dtype (the
+ * input's format or SC5_F32) with the library's pitch (rows rounded up to
+ * 16 bytes).  The first step converts in_dtype to out_dtype with the given
+ * scales; later steps keep out_dtype and its scale.  Every level that is
+ * reduced must be at least 5 x 5. */
+typedef struct {
+    int32_t planes, H, W;
+    int64_t in_pitch;          /* elements; in_pitch * element size a multiple of 16 */
+    int32_t in_dtype, out_dtype;
+    int32_t levels;            /* REDUCE steps, >= 1 */
+} sc5_pyramid_desc;
+
+typedef struct sc5_pyramid_s *sc5_pyramid;
+
+/* Validate and build one REDUCE plan per step (no device allocation). */
+SC5_API sc5_status sepconv5_pyramid_create(const sc5_pyramid_desc *desc, sc5_pyramid *out);
+/* Size of level `level` (0 = the input, 1..levels = the steps' results):
+ * rows, columns and row pitch in elements of its format.  A caller allocates
+ * level l >= 1 as planes * H * pitch elements. */
+SC5_API sc5_status sepconv5_pyramid_level(sc5_pyramid pyr, int32_t level, int32_t *H, int32_t *W,
+                                          int64_t *pitch);
+/* Run the steps in order on `stream`: in (dev, level 0), levels (host array of
+ * `levels` dev pointers, levels[l-1] receives level l, 16-byte aligned), k
+ * (host, 5 taps, used at every step).  Asynchronous. */
+SC5_API sc5_status sepconv5_pyramid_run(sc5_pyramid pyr, const void *in, void *const *levels, const float k[5],
+                                        float in_scale, float out_scale, void *stream);
+SC5_API sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Run many images of different sizes and kernels in one persistent launch

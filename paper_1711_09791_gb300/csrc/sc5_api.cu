@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -486,6 +487,106 @@ extern "C" sc5_status sepconv5_plan_info(sc5_plan p, int32_t *tile_h, int32_t *t
     if (tile_w) *tile_w = p->shape.tile_w;
     if (stages) *stages = p->shape.stages;
     if (ctas_per_sm) *ctas_per_sm = p->ctas_per_sm;
+    return SC5_OK;
+}
+
+// ------------------------------------------------------------------ pyramids
+
+struct sc5_pyramid_s {
+    sc5_pyramid_desc d{};
+    std::vector<sc5_plan> plans;       // step l reduces level l to level l+1
+    std::vector<int32_t> h, w;         // level sizes, 0..levels
+    std::vector<int64_t> pitch;        // level pitches (elements of their format)
+};
+
+extern "C" sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr);
+
+extern "C" sc5_status sepconv5_pyramid_create(const sc5_pyramid_desc *desc, sc5_pyramid *out)
+{
+    clear_error();
+    if (!desc || !out) return fail(SC5_EINVAL, "null argument");
+    *out = nullptr;
+    const sc5_pyramid_desc &d = *desc;
+    if (d.levels < 1 || d.levels > 30) return fail(SC5_EINVAL, "levels must be 1..30 (got %d)", d.levels);
+    if (d.out_dtype != d.in_dtype && d.out_dtype != SC5_F32)
+        return fail(SC5_EINVAL, "pyramid levels are stored in the input's format or FP32");
+    std::unique_ptr<sc5_pyramid_s> p(new (std::nothrow) sc5_pyramid_s);
+    if (!p) return fail(SC5_ENOMEM, "host allocation failed");
+    p->d = d;
+    p->h.push_back(d.H);
+    p->w.push_back(d.W);
+    p->pitch.push_back(d.in_pitch);
+    const int eo = dtype_bytes(d.out_dtype);
+    if (!eo) return fail(SC5_EINVAL, "unknown dtype %d", d.out_dtype);
+    for (int l = 0; l < d.levels; ++l) {
+        const int H = p->h.back(), W = p->w.back();
+        if (H < 5 || W < 5) {
+            sepconv5_pyramid_destroy(p.release());
+            return fail(SC5_EINVAL, "level %d is %d x %d: too small for another step", l, H, W);
+        }
+        const int Ho = (H - kHalo + 1) / 2, Wo = (W - kHalo + 1) / 2;
+        const int64_t op = (static_cast<int64_t>(Wo) * eo + 15) / 16 * 16 / eo;
+        sc5_plan_desc pd{};
+        pd.planes = d.planes;
+        pd.H = H;
+        pd.W = W;
+        pd.in_pitch = p->pitch.back();
+        pd.out_pitch = op;
+        pd.in_dtype = l == 0 ? d.in_dtype : d.out_dtype;
+        pd.out_dtype = d.out_dtype;
+        pd.border = SC5_BORDER_VALID;
+        pd.algo = SC5_ALGO_REDUCE;
+        pd.taps = kTaps;
+        sc5_plan plan = nullptr;
+        const sc5_status st = sepconv5_plan(&pd, &plan);
+        if (st != SC5_OK) {
+            const std::string msg = sepconv5_last_error();  // cleanup clears it
+            sepconv5_pyramid_destroy(p.release());
+            return fail(st, "level %d: %s", l, msg.c_str());
+        }
+        p->plans.push_back(plan);
+        p->h.push_back(Ho);
+        p->w.push_back(Wo);
+        p->pitch.push_back(op);
+    }
+    *out = p.release();
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_pyramid_level(sc5_pyramid pyr, int32_t level, int32_t *H, int32_t *W,
+                                             int64_t *pitch)
+{
+    clear_error();
+    if (!pyr) return fail(SC5_EINVAL, "null pyramid");
+    if (level < 0 || level > pyr->d.levels) return fail(SC5_EINVAL, "level %d outside 0..%d", level, pyr->d.levels);
+    if (H) *H = pyr->h[level];
+    if (W) *W = pyr->w[level];
+    if (pitch) *pitch = pyr->pitch[level];
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_pyramid_run(sc5_pyramid pyr, const void *in, void *const *levels, const float k[5],
+                                           float in_scale, float out_scale, void *stream)
+{
+    clear_error();
+    if (!pyr || !in || !levels || !k) return fail(SC5_EINVAL, "null argument");
+    const void *src = in;
+    for (int l = 0; l < pyr->d.levels; ++l) {
+        if (!levels[l]) return fail(SC5_EINVAL, "levels[%d] is null", l);
+        const float is = l == 0 ? in_scale : out_scale;
+        const sc5_status st = sepconv5_run(pyr->plans[l], src, levels[l], k, is, out_scale, stream);
+        if (st != SC5_OK) return st;
+        src = levels[l];
+    }
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr)
+{
+    clear_error();
+    if (!pyr) return SC5_OK;
+    for (sc5_plan p : pyr->plans) sepconv5_plan_destroy(p);
+    delete pyr;
     return SC5_OK;
 }
 

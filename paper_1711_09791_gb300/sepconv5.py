@@ -48,6 +48,11 @@ class Image(ctypes.Structure):
                 ("in_scale", c_float), ("out_scale", c_float)]
 
 
+class PyramidDesc(ctypes.Structure):
+    _fields_ = [("planes", c_int32), ("H", c_int32), ("W", c_int32), ("in_pitch", c_int64),
+                ("in_dtype", c_int32), ("out_dtype", c_int32), ("levels", c_int32)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_size_t), ("max_inflight", c_int32), ("dtype", c_int32),
                 ("planes", c_int32), ("n_streams", c_int32), ("max_merge", c_int32), ("merge", c_int32),
@@ -96,6 +101,10 @@ def load(path: str = LIB_PATH):
                                  POINTER(c_int32), POINTER(c_int32)],
         "sepconv5_tune_lookup_batch": [c_int32, c_int32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32),
                                  POINTER(c_int32), POINTER(c_int32)],
+        "sepconv5_pyramid_create": [POINTER(PyramidDesc), POINTER(V)],
+        "sepconv5_pyramid_level": [V, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64)],
+        "sepconv5_pyramid_run": [V, V, POINTER(c_void_p), POINTER(c_float), c_float, c_float, V],
+        "sepconv5_pyramid_destroy": [V],
         "serve_create": [POINTER(ServeCfg), POINTER(V)],
         "serve_submit": [V, POINTER(Image), POINTER(c_uint64)],
         "serve_poll": [V, c_uint64, c_int32, POINTER(c_double)],
@@ -339,6 +348,47 @@ def selftest_wait_timeout(limit_us: int, stream=None):
 
 def launch_count() -> int:
     return load().sepconv5_launch_count()
+
+
+class Pyramid:
+    """`levels` chained REDUCE steps of a planar image (sepconv5_pyramid_*).
+    level(l) gives (H, W, pitch) of level l (0 = the input); run() fills the
+    caller's level buffers, levels[l-1] holding level l."""
+
+    def __init__(self, planes: int, H: int, W: int, in_pitch: int | None = None, in_dtype="f32",
+                 out_dtype=None, levels: int = 1):
+        d = PyramidDesc()
+        d.planes, d.H, d.W = planes, H, W
+        d.in_pitch = W if in_pitch is None else in_pitch
+        d.in_dtype = _dt(in_dtype)
+        d.out_dtype = _dt(in_dtype if out_dtype is None else out_dtype)
+        d.levels = levels
+        h = c_void_p()
+        _check(load().sepconv5_pyramid_create(byref(d), byref(h)), "sepconv5_pyramid_create")
+        self._h = h
+        self.levels = levels
+
+    def level(self, level: int) -> tuple[int, int, int]:
+        H, W, pitch = c_int32(), c_int32(), c_int64()
+        _check(load().sepconv5_pyramid_level(self._h, level, byref(H), byref(W), byref(pitch)),
+               "sepconv5_pyramid_level")
+        return H.value, W.value, pitch.value
+
+    def run(self, src, levels, k, in_scale=1.0, out_scale=1.0, stream=None):
+        ptrs = (c_void_p * len(levels))(*[_ptr(t) for t in levels])
+        _check(load().sepconv5_pyramid_run(self._h, _ptr(src), ptrs, _taps(k), in_scale, out_scale,
+                                           _stream(stream)), "sepconv5_pyramid_run")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sepconv5_pyramid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -176,3 +176,54 @@ def test_unsupported_reduce_plans_and_calls_refused(sc5):
         plan.run_host(A, out, [0, 0, 1, 0, 0])
     assert plan.info()["tile_w"] == 128
     plan.close()
+
+
+@pytest.mark.parametrize("in_dtype,out_dtype", [("f32", "f32"), ("bf16", "f32"), ("bf16", "bf16")])
+def test_pyramid_api_matches_chained_plans(sc5, in_dtype, out_dtype):
+    """sepconv5_pyramid_*: level sizes and pitches, and every level bitwise the
+    result of chaining REDUCE plans by hand; FP32 levels also against the
+    oracle's steps on the original image."""
+    import torch
+    H = W = 530
+    x = synth.image(23, H, W)
+    padded, scale = _stored(x, in_dtype)
+    pitch = padded.shape[2]
+    k = synth.kernel_normalised(23)
+    out_scale = 1.0 if out_dtype == "f32" else scale
+    A_dev = U.to_dev(padded)
+    pyr = sc5.Pyramid(3, H, W, pitch, in_dtype, out_dtype, levels=4)
+    assert pyr.level(0) == (H, W, pitch)
+    bufs = []
+    for lv in range(1, 5):
+        h, w, p = pyr.level(lv)
+        assert (h, w) == sc5.reduce_dims(*pyr.level(lv - 1)[:2])
+        assert (p * sc5.DTYPE_BYTES[out_dtype]) % 16 == 0 and p >= w
+        bufs.append(U.empty_dev((3, h, p), out_dtype))
+    pyr.run(A_dev, bufs, k, scale, out_scale)
+    torch.cuda.synchronize()
+    assert sc5.device_status() == 0
+    pyr.close()
+    cur, h, w, p, dt, s_in = A_dev, H, W, pitch, in_dtype, scale
+    ref = U.decode(padded[:, :, :W], in_dtype, scale)
+    for lv, buf in enumerate(bufs, start=1):
+        want, out = _reduce(sc5, cur, h, w, p, k, dt, out_dtype, s_in, out_scale)
+        got = U.from_dev(buf, out_dtype)[:, :, :want.shape[2]]
+        assert np.array_equal(got, want), lv
+        ref = oracle.reduce2(ref, k)
+        if out_dtype == "f32":
+            assert U.max_abs(got, ref) <= lv * U.FP32_TOL, lv
+        cur, p, dt, s_in = out, out.shape[2], out_dtype, out_scale
+        h, w = want.shape[1], want.shape[2]
+
+
+def test_pyramid_refusals(sc5):
+    with pytest.raises(sc5.Sepconv5Error) as e:
+        sc5.Pyramid(3, 40, 40, 40, "f32", levels=4)  # 40 -> 18 -> 7 -> 2: level 3 is too small to reduce
+    assert e.value.status == sc5.EINVAL
+    with pytest.raises(sc5.Sepconv5Error):
+        sc5.Pyramid(3, 64, 64, 64, "f32", "bf16", levels=1)  # levels in the input's format or FP32
+    pyr = sc5.Pyramid(3, 40, 40, 40, "f32", levels=3)
+    assert pyr.level(3) == (2, 2, 4)
+    with pytest.raises(sc5.Sepconv5Error):
+        pyr.level(4)
+    pyr.close()
