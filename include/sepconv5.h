@@ -312,6 +312,14 @@ SC5_API sc5_status sepconv5_pyramid_level(sc5_pyramid pyr, int32_t level, int32_
  * (host, 5 taps, used at every step).  Asynchronous. */
 SC5_API sc5_status sepconv5_pyramid_run(sc5_pyramid pyr, const void *in, void *const *levels, const float k[5],
                                         float in_scale, float out_scale, void *stream);
+/* Record sepconv5_pyramid_run for these buffers, taps and scales into a
+ * CUDA graph kept by the pyramid (replacing any earlier one), so that the
+ * small levels cost no per-launch host work: sepconv5_pyramid_replay then
+ * runs it on `stream`.  The buffers must stay valid and keep their addresses
+ * while the graph is used.  Nothing runs at capture time. */
+SC5_API sc5_status sepconv5_pyramid_capture(sc5_pyramid pyr, const void *in, void *const *levels, const float k[5],
+                                            float in_scale, float out_scale);
+SC5_API sc5_status sepconv5_pyramid_replay(sc5_pyramid pyr, void *stream);
 SC5_API sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr);
 
 /* ---------------------------------------------------------------- batches */

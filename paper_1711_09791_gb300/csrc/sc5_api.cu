@@ -497,6 +497,8 @@ struct sc5_pyramid_s {
     std::vector<sc5_plan> plans;       // step l reduces level l to level l+1
     std::vector<int32_t> h, w;         // level sizes, 0..levels
     std::vector<int64_t> pitch;        // level pitches (elements of their format)
+    cudaGraph_t graph = nullptr;       // sepconv5_pyramid_capture
+    cudaGraphExec_t exec = nullptr;
 };
 
 extern "C" sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr);
@@ -581,10 +583,53 @@ extern "C" sc5_status sepconv5_pyramid_run(sc5_pyramid pyr, const void *in, void
     return SC5_OK;
 }
 
+extern "C" sc5_status sepconv5_pyramid_capture(sc5_pyramid pyr, const void *in, void *const *levels,
+                                               const float k[5], float in_scale, float out_scale)
+{
+    clear_error();
+    if (!pyr || !in || !levels || !k) return fail(SC5_EINVAL, "null argument");
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail_cuda(e, "capture stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sc5_status st = SC5_OK;
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+        st = sepconv5_pyramid_run(pyr, in, levels, k, in_scale, out_scale, cs);
+        const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        if (st == SC5_OK && ee != cudaSuccess) e = ee;
+    }
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess && st == SC5_OK) e = cudaGraphInstantiate(&x, g, 0);
+    cudaStreamDestroy(cs);
+    if (st != SC5_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != SC5_OK ? st : fail_cuda(e, "pyramid graph capture");
+    }
+    if (pyr->exec) cudaGraphExecDestroy(pyr->exec);
+    if (pyr->graph) cudaGraphDestroy(pyr->graph);
+    pyr->graph = g;
+    pyr->exec = x;
+    return SC5_OK;
+}
+
+extern "C" sc5_status sepconv5_pyramid_replay(sc5_pyramid pyr, void *stream)
+{
+    clear_error();
+    if (!pyr) return fail(SC5_EINVAL, "null pyramid");
+    if (!pyr->exec) return fail(SC5_EINVAL, "nothing captured: call sepconv5_pyramid_capture first");
+    const cudaError_t e = cudaGraphLaunch(pyr->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(e, "pyramid graph launch");
+    note_launches(pyr->d.levels);
+    return SC5_OK;
+}
+
 extern "C" sc5_status sepconv5_pyramid_destroy(sc5_pyramid pyr)
 {
     clear_error();
     if (!pyr) return SC5_OK;
+    if (pyr->exec) cudaGraphExecDestroy(pyr->exec);
+    if (pyr->graph) cudaGraphDestroy(pyr->graph);
     for (sc5_plan p : pyr->plans) sepconv5_plan_destroy(p);
     delete pyr;
     return SC5_OK;

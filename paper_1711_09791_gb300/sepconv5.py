@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
         "sepconv5_pyramid_create": [POINTER(PyramidDesc), POINTER(V)],
         "sepconv5_pyramid_level": [V, c_int32, POINTER(c_int32), POINTER(c_int32), POINTER(c_int64)],
         "sepconv5_pyramid_run": [V, V, POINTER(c_void_p), POINTER(c_float), c_float, c_float, V],
+        "sepconv5_pyramid_capture": [V, V, POINTER(c_void_p), POINTER(c_float), c_float, c_float],
+        "sepconv5_pyramid_replay": [V, V],
         "sepconv5_pyramid_destroy": [V],
         "serve_create": [POINTER(ServeCfg), POINTER(V)],
         "serve_submit": [V, POINTER(Image), POINTER(c_uint64)],
@@ -378,6 +380,16 @@ class Pyramid:
         ptrs = (c_void_p * len(levels))(*[_ptr(t) for t in levels])
         _check(load().sepconv5_pyramid_run(self._h, _ptr(src), ptrs, _taps(k), in_scale, out_scale,
                                            _stream(stream)), "sepconv5_pyramid_run")
+
+    def capture(self, src, levels, k, in_scale=1.0, out_scale=1.0):
+        """Record run() for these buffers into a CUDA graph (sepconv5_pyramid_capture)."""
+        self._keep = (src, list(levels))  # the graph holds their addresses
+        ptrs = (c_void_p * len(levels))(*[_ptr(t) for t in levels])
+        _check(load().sepconv5_pyramid_capture(self._h, _ptr(src), ptrs, _taps(k), in_scale, out_scale),
+               "sepconv5_pyramid_capture")
+
+    def replay(self, stream=None):
+        _check(load().sepconv5_pyramid_replay(self._h, _stream(stream)), "sepconv5_pyramid_replay")
 
     def close(self):
         if getattr(self, "_h", None):

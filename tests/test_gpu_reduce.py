@@ -216,6 +216,31 @@ def test_pyramid_api_matches_chained_plans(sc5, in_dtype, out_dtype):
         h, w = want.shape[1], want.shape[2]
 
 
+def test_pyramid_graph_replay_matches_run(sc5):
+    import torch
+    H = W = 700
+    A = U.to_dev(synth.image(31, H, W, pitch=U.pitch_for(W, "f32")))
+    k = synth.kernel_normalised(31)
+    pyr = sc5.Pyramid(3, H, W, U.pitch_for(W, "f32"), "f32", levels=3)
+    shapes = [pyr.level(lv) for lv in range(1, 4)]
+    run_bufs = [U.empty_dev((3, h, p), "f32") for h, w, p in shapes]
+    graph_bufs = [U.empty_dev((3, h, p), "f32") for h, w, p in shapes]
+    with pytest.raises(sc5.Sepconv5Error):
+        pyr.replay()  # nothing captured yet
+    pyr.run(A, run_bufs, k)
+    pyr.capture(A, graph_bufs, k)
+    torch.cuda.synchronize()
+    for b in graph_bufs:  # capturing ran nothing
+        assert U.sentinel_intact(U.from_dev(b, "f32"), "f32")
+    pyr.replay()
+    pyr.replay()
+    torch.cuda.synchronize()
+    assert sc5.device_status() == 0
+    for (h, w, p), a, b in zip(shapes, run_bufs, graph_bufs):
+        assert np.array_equal(U.from_dev(a, "f32")[:, :, :w], U.from_dev(b, "f32")[:, :, :w])
+    pyr.close()
+
+
 def test_pyramid_refusals(sc5):
     with pytest.raises(sc5.Sepconv5Error) as e:
         sc5.Pyramid(3, 40, 40, 40, "f32", levels=4)  # 40 -> 18 -> 7 -> 2: level 3 is too small to reduce
