@@ -293,12 +293,13 @@ static bool hwc_lookup(int in_dtype, int out_dtype, HwcEntry *e)
     // (BF16 0.19 against 0.15 ms) and keep 4 rows.
     static const HwcEntry f32_f32 = hwc_entry<float, float, 32, 2, 3>();
     static const HwcEntry bf_bf = hwc_entry<bf16_t, bf16_t, 64, 4, 3>();
-    // 16-bit to FP32 is closer to HBM-bound and takes FP32's 2-row strips
-    // (BF16 -> FP32: 0.208 ms against 0.231 ms for 64/4/3); FP8 -> FP32 keeps
-    // 64/4/5 (0.187 against 0.240 ms with 32/2/8)
+    // BF16 -> FP32 is closer to HBM-bound and takes FP32's 2-row strips (0.208
+    // ms against 0.231 ms for 64/4/3); FP16 -> FP32 (its widening costs more)
+    // gains nothing there (0.228 against 0.226 ms) and FP8 -> FP32 loses (0.240
+    // against 0.187 ms): both keep 4-row strips
     static const HwcEntry bf_f32 = hwc_entry<bf16_t, float, 32, 2, 6>();
     static const HwcEntry h_h = hwc_entry<f16_t, f16_t, 64, 4, 3>();
-    static const HwcEntry h_f32 = hwc_entry<f16_t, float, 32, 2, 6>();
+    static const HwcEntry h_f32 = hwc_entry<f16_t, float, 64, 4, 3>();
     static const HwcEntry e_e = hwc_entry<fp8e4m3_t, fp8e4m3_t, 64, 4, 5>();
     static const HwcEntry e_f32 = hwc_entry<fp8e4m3_t, float, 64, 4, 5>();
     const HwcEntry *r = nullptr;
