@@ -487,22 +487,27 @@ def leg_serve(sc5, synth, n_req):
                          max_merge=8 if merge else 0)
         stream_ = synth.serve_stream(seed, n, rate) if rate else [(0.0, c, s) for (_, c, s) in synth.serve_stream(seed, n, 1.0)]
         lat = []
-        tickets = _q.Queue()
+        # one poller per size class: requests of one size finish in order, so a
+        # large request in flight does not hold back the buffers of small ones
+        tickets = [_q.Queue() for _ in pool]
         px_done = [0]
+        lock = _t.Lock()
 
-        def poller():
+        def poller(tq):
             while True:
-                item = tickets.get()
+                item = tq.get()
                 if item is None:
                     return
                 t, t_arr, t_sub, buf, q, px = item
                 l_srv = srv.poll(t, -1)
-                lat.append((t_sub + l_srv * 1e-6) - t_arr)
-                px_done[0] += px
+                with lock:
+                    lat.append((t_sub + l_srv * 1e-6) - t_arr)
+                    px_done[0] += px
                 q.put(buf)
 
-        th = _t.Thread(target=poller)
-        th.start()
+        ths = [_t.Thread(target=poller, args=(tq,)) for tq in tickets]
+        for th in ths:
+            th.start()
         t_start = time.perf_counter()
         for (t_arr, ci, kseed) in stream_:
             src, q, h, w = pool[ci]
@@ -521,9 +526,11 @@ def leg_serve(sc5, synth, n_req):
             while tk is None:
                 time.sleep(1e-4)
                 tk = srv.submit(req)
-            tickets.put((tk, target, t_sub, buf, q, h * w))
-        tickets.put(None)
-        th.join()
+            tickets[ci].put((tk, target, t_sub, buf, q, h * w))
+        for tq in tickets:
+            tq.put(None)
+        for th in ths:
+            th.join()
         wall = time.perf_counter() - t_start
         st = srv.stats()
         srv.close()
