@@ -32,7 +32,11 @@ def test_default_not_slower_than_one_cta_per_sm():
     th, tw, st = sc5.fused_configs("bf16")[0]
     default = sc5.Plan(3, H, W, W, W - 4, "bf16")
     one = sc5.Plan(3, H, W, W, W - 4, "bf16", tile_h=th, tile_w=tw, stages=st, ctas_per_sm=1)
-    t_default, t_one = _time(sc5, default, A, out, k), _time(sc5, one, A, out, k)
+    # interleaved repeats, fastest of each: robust to a noisy neighbour on the GPU
+    t_default, t_one = [], []
+    for _ in range(3):
+        t_default.append(_time(sc5, default, A, out, k, reps=20))
+        t_one.append(_time(sc5, one, A, out, k, reps=20))
     default.close()
     one.close()
-    assert t_default <= t_one * 1.02, (t_default, t_one)
+    assert min(t_default) <= min(t_one) * 1.02, (t_default, t_one)
