@@ -229,7 +229,8 @@ SC5_API sc5_status sepconv5_run_inplace(sc5_plan plan, void *img, const float k[
  * the kernel of band b and the copy of band b-1 back overlap on three
  * streams.  Device staging buffers (input and output image) are allocated by
  * the plan on first use and kept until it is destroyed.  Returns when the
- * result is in host_out.  Fused form only; `stream` carries the kernels. */
+ * result is in host_out; only the output values of each row are written (the
+ * row padding of host_out is left as it was).  `stream` carries the kernels. */
 SC5_API sc5_status sepconv5_run_host(sc5_plan plan, const void *host_in, void *host_out, const float k[5],
                                      float in_scale, float out_scale, void *stream);
 
@@ -424,7 +425,8 @@ SC5_API sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out);
 
 /* Queue one request.  req->in and req->out are HOST pointers to
  * [planes][H][pitch] images of the server's dtype; the server reads `in`
- * and writes `out` asynchronously, so both must stay valid until serve_poll
+ * and writes the W-4 output values of each row of `out` (its row padding is
+ * left as it was) asynchronously, so both must stay valid until serve_poll
  * returns SC5_OK for the ticket (pinned memory gives the fastest copies).
  * Returns SC5_EAGAIN when the request could never fit the budget together
  * with what is queued (backpressure: retry later), SC5_EINVAL for bad shapes. */

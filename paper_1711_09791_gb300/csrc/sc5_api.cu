@@ -829,7 +829,9 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
         if (e != cudaSuccess) return fail_cuda(e, "copy to device");
         st = sepconv5_run(p, din, dout, k, in_scale, out_scale, stream);
         if (st != SC5_OK) return st;
-        e = cudaMemcpyAsync(hout_c, dout, out_bytes, cudaMemcpyDeviceToHost, s);
+        // the output rows' valid values only: the caller's row padding stays as it was
+        e = cudaMemcpy2DAsync(hout_c, out_row, dout, out_row, static_cast<size_t>(d.border == SC5_BORDER_KEEP ? d.W : d.W - kHalo) * eo,
+                              static_cast<size_t>(d.planes) * hout, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         return e == cudaSuccess ? SC5_OK : fail_cuda(e, "copy to host");
     }
@@ -888,7 +890,8 @@ extern "C" sc5_status sepconv5_run_host(sc5_plan p, const void *host_in, void *h
             cudaEventRecord(kev, s);
             cudaStreamWaitEvent(p->s_out, kev, 0);
             const size_t off = out_plane + out_row * y0;
-            e = cudaMemcpyAsync(hout_c + off, dout + off, out_row * rows_out, cudaMemcpyDeviceToHost, p->s_out);
+            e = cudaMemcpy2DAsync(hout_c + off, out_row, dout + off, out_row, static_cast<size_t>(d.W - kHalo) * eo,
+                                  rows_out, cudaMemcpyDeviceToHost, p->s_out);
             if (e != cudaSuccess) return fail_cuda(e, "band copy to host");
         }
     }

@@ -332,10 +332,14 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
         cudaEvent_t kdone = get_event();
         cudaEventRecord(kdone, cs);
         cudaStreamWaitEvent(s_d2h, kdone, 0);
-        for (auto &r : group)
-            cudaMemcpyAsync(r->img.out, arena_base + r->out_off,
-                            static_cast<size_t>(cfg.planes) * (r->img.H - 4) * r->img.out_pitch * es,
-                            cudaMemcpyDeviceToHost, s_d2h);
+        // results go back as their W-4 valid values per row: the caller's row
+        // padding is left as it was, as sepconv5_run leaves it
+        for (auto &r : group) {
+            const size_t pitch_b = static_cast<size_t>(r->img.out_pitch) * es;
+            cudaMemcpy2DAsync(r->img.out, pitch_b, arena_base + r->out_off, pitch_b,
+                              static_cast<size_t>(r->img.W - 4) * es,
+                              static_cast<size_t>(cfg.planes) * (r->img.H - 4), cudaMemcpyDeviceToHost, s_d2h);
+        }
         cudaEventRecord(L.done, s_d2h);
         put_event(kdone);  // its record/wait are already enqueued
     } else {
