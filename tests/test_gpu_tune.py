@@ -2,7 +2,6 @@
 table round-trips through its JSON file, and plans pick the tuned shape."""
 import json
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

@@ -29,7 +29,6 @@ What each pin fixes:
 A last test plants plausible mistakes in copies of the C source and checks
 that at least one pin fails for each.
 """
-import ctypes
 import math
 import os
 import shutil
