@@ -76,7 +76,49 @@ static int gpu_checks(void)
                     fprintf(stderr, "mismatch at %d %d %d\n", pl, y, x);
                     return 1;
                 }
+    int32_t th = 0, tw = 0, st = 0, ctas = 0;
+    if (sepconv5_plan_info(p, &th, &tw, &st, &ctas) != SC5_OK || th < 1 || tw < 1 || st < 1 || ctas < 1) return 1;
     sepconv5_plan_destroy(p);
+
+    /* one REDUCE step through the pyramid calls: with the centre tap alone the
+       level is the input at every second row and column from (2, 2) */
+    sc5_pyramid_desc pd;
+    memset(&pd, 0, sizeof pd);
+    pd.planes = P;
+    pd.H = H;
+    pd.W = W;
+    pd.in_pitch = pitch;
+    pd.in_dtype = pd.out_dtype = SC5_F32;
+    pd.levels = 1;
+    sc5_pyramid pyr = NULL;
+    if (sepconv5_pyramid_create(&pd, &pyr) != SC5_OK) {
+        fprintf(stderr, "pyramid: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    int32_t h1 = 0, w1 = 0;
+    int64_t p1 = 0;
+    if (sepconv5_pyramid_level(pyr, 1, &h1, &w1, &p1) != SC5_OK) return 1;
+    if (h1 != (H - 3) / 2 || w1 != (W - 3) / 2 || p1 < w1 || (p1 * 4) % 16) return 1;
+    float *dl = NULL;
+    if (cudaMalloc((void **)&dl, (size_t)P * h1 * p1 * sizeof(float)) != cudaSuccess) return 1;
+    void *levels[1] = {dl};
+    if (sepconv5_pyramid_run(pyr, da, levels, k, 1.f, 1.f, NULL) != SC5_OK) {
+        fprintf(stderr, "pyramid run: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    if (sepconv5_device_status(NULL, &code) != SC5_OK) return 1;
+    float *l = (float *)malloc((size_t)P * h1 * p1 * sizeof(float));
+    cudaMemcpy(l, dl, (size_t)P * h1 * p1 * sizeof(float), cudaMemcpyDeviceToHost);
+    for (int pl = 0; pl < P; ++pl)
+        for (int y = 0; y < h1; ++y)
+            for (int x = 0; x < w1; ++x)
+                if (l[((size_t)pl * h1 + y) * p1 + x] != a[((size_t)pl * H + 2 * y + 2) * pitch + 2 * x + 2]) {
+                    fprintf(stderr, "pyramid mismatch at %d %d %d\n", pl, y, x);
+                    return 1;
+                }
+    sepconv5_pyramid_destroy(pyr);
+    free(l);
+    cudaFree(dl);
     cudaFree(da);
     cudaFree(db);
     free(a);

@@ -1,7 +1,8 @@
 """The C ABI from plain C: tests/c/abi_example.c includes only sepconv5.h
 (and the CUDA runtime), is compiled with gcc and linked against
 libsepconv5.so.  Host-only calls run without a GPU; the GPU variant checks
-an identity convolution bit for bit."""
+an identity convolution bit for bit, the plan's reported launch
+configuration, and one pyramid REDUCE step (level sizes, pitch, values)."""
 import os
 import subprocess
 import tempfile
