@@ -6,11 +6,12 @@
 // resident arena (a fixed device allocation of hbm_budget_bytes made at
 // start) has room for their input and output and fewer than max_inflight
 // are admitted; each admitted request's input is copied to the device on a
-// copy stream.  Whatever has been admitted and not yet launched is merged
-// into ONE persistent launch of the fused batch kernel (per-image
-// descriptors + tile work-list), issued on the next of n_streams compute
-// streams after the request's copy has landed; its outputs are copied back to
-// the requests' host buffers on a second copy stream.  At most two launches
+// copy stream.  What has been admitted and not yet launched is merged, up to
+// max_merge requests at a time, into one persistent launch of the fused batch
+// kernel (per-image descriptors + tile work-list), issued on the next of
+// n_streams compute streams after the requests' copies have landed; the
+// output values (not the rows' padding) are copied back to the requests' host
+// buffers on a second copy stream.  At most two launches
 // per compute stream are in flight: while they run, newly arriving requests
 // are admitted and staged, and go out together in the next launch.  A
 // completion thread retires launches as their last copy lands, frees their
