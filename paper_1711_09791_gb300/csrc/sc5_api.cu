@@ -1,16 +1,18 @@
 // sc5_api.cu -- the C ABI of libsepconv5: plans (validation, TMA tensor
-// maps, tile grid), single-image runs of both forms, batches with a tile
-// work-list (one-shot or captured in a CUDA graph), the device status word,
-// the empty-launch probe and the launch counter.
+// maps, tile grid, launch configuration), single-image runs of every form
+// (fused, two-pass, direct, HWC, pyramid REDUCE step), the in-place and
+// offload calls, pyramids (chained REDUCE plans, optionally a CUDA graph),
+// batches with a tile work-list (one-shot or captured in a CUDA graph), the
+// device status word, the empty-launch probe and the launch counter.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
-#include <memory>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
