@@ -5,7 +5,13 @@ time: a command-line tool for measuring (or profiling) a single case.
 
 Pixels are uniform in [0, 255) (seed 2), k is five seeded uniform values
 normalised to sum 1; FP8 inputs use the scale 448/max.  Prints one JSON line
-with the median kernel time (CUDA events) and the achieved algorithmic GB/s.
+with the median kernel time (CUDA events) and the achieved algorithmic GB/s
+(input read once plus output written once).
+
+Options: --algo fused | two_pass | direct | reduce (one pyramid REDUCE step),
+--layout planar | hwc, --tile TH,TW,STAGES (a compiled shape; TH and STAGES
+for reduce), --ctas N (CTAs per SM; 0 = the planner's choice), --planes, --H,
+--W, --reps, --warmup.
 """
 from __future__ import annotations
 
