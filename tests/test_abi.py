@@ -2,10 +2,13 @@
 exports every function the public header declares, and rejects bad
 descriptors before touching the device."""
 import ctypes
+import os
 
 import pytest
 
 from paper_1711_09791_gb300 import build as sc5_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -51,3 +54,16 @@ def test_bad_descriptors_rejected_on_host(sc5, kw):
 def test_tune_lookup_defaults_without_table(sc5):
     cfg, found = sc5.tune_lookup("f32", "f32", 8192, 8192)
     assert not found and cfg["tile_w"] == 128
+
+
+def test_header_compiles_as_c_and_cpp_alone(tmp_path):
+    """include/sepconv5.h is self-contained: a translation unit that includes
+    only it compiles as C11 and as C++17 (no CUDA headers needed)."""
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    src_c = tmp_path / "h.c"
+    src_c.write_text('#include "sepconv5.h"\nint main(void) { sc5_plan_desc d; (void)d; return (int)SC5_OK; }\n')
+    src_cpp = tmp_path / "h.cpp"
+    src_cpp.write_text('#include "sepconv5.h"\nint main() { sc5_pyramid_desc d{}; return d.levels; }\n')
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src_c)])
+    subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src_cpp)])
