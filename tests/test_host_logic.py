@@ -2,6 +2,7 @@
 conversions (checked against the oracle's pinned decoders), the benchmark's
 helpers, and the binding's argument checks."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -91,3 +92,27 @@ def test_binding_header_and_arguments():
     assert len(sepconv5._taps([1, 2, 3], 3)) == 3
     assert sepconv5._ptr(None) is None and sepconv5._ptr(1234) == 1234
     assert math.isclose(sepconv5.DTYPE_BYTES["fp8e4m3"], 1)
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference on the host: one JSON line with the contract's
+    keys, the same config object as the GPU arm, and the oracle as its CPU
+    baseline."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "Mpix/s"
+    assert d["config"] == bench.run_config(1)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
