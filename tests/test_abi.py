@@ -67,3 +67,49 @@ def test_header_compiles_as_c_and_cpp_alone(tmp_path):
     src_cpp.write_text('#include "sepconv5.h"\nint main() { sc5_pyramid_desc d{}; return d.levels; }\n')
     subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src_c)])
     subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, str(src_cpp)])
+
+
+def test_tune_table_load_and_lookup(sc5, tmp_path):
+    """A tuning table read by sepconv5_tune_load: entries are found by the size
+    class of the plane area (one class per factor of 4 from 2^14 pixels) and by
+    kernel kind, an entry naming a shape that is not compiled is dropped, and a
+    table written for another GPU is refused.  Without a device the table key
+    is the name "unknown"."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the table key is the device's name; this test writes the no-device key")
+    cfgs = sc5.fused_configs("f32", "f32")
+    (th1, tw1, st1), (th2, tw2, st2) = cfgs[0], cfgs[1]
+
+    def entry(kind, cls, th, tw, st, ctas):
+        return (f' {{"in": 0, "out": 0, "kind": {kind}, "cls": {cls}, "tile_h": {th}, "tile_w": {tw}, '
+                f'"stages": {st}, "ctas": {ctas}, "us": 1.000}}')
+
+    def write(gpu, entries):
+        p = tmp_path / f"{gpu.replace(' ', '_')}.json"
+        p.write_text('{"gpu": "%s", "entries": [\n' % gpu + ",\n".join(entries) + "\n]}\n")
+        return str(p)
+
+    try:
+        sc5.autotune(0, [])
+        table = write("unknown", [entry(0, 2, th1, tw1, st1, 2), entry(1, 2, th2, tw2, st2, 1),
+                                  entry(0, 4, 24, 128, 3, 1)])
+        sc5.tune_load(table)
+        # 256 x 256 = 2^16 and 300 x 300 (log2 = 16.5) are class 2; 64 x 64 is class 0
+        for H, W in ((256, 256), (300, 300)):
+            cfg, found = sc5.tune_lookup("f32", "f32", H, W)
+            assert found and (cfg["tile_h"], cfg["tile_w"], cfg["stages"], cfg["ctas_per_sm"]) == (th1, tw1, st1, 2)
+            cfg, found = sc5.tune_lookup("f32", "f32", H, W, batch=True)
+            assert found and (cfg["tile_h"], cfg["tile_w"], cfg["stages"], cfg["ctas_per_sm"]) == (th2, tw2, st2, 1)
+        assert not sc5.tune_lookup("f32", "f32", 64, 64)[1]
+        assert not sc5.tune_lookup("bf16", "bf16", 256, 256)[1]
+        # class 4 (2^20 .. 2^22 pixels) named a 24-row tile, which is not compiled
+        cfg, found = sc5.tune_lookup("f32", "f32", 1024, 2048)
+        assert not found and cfg["ctas_per_sm"] == 0
+        with pytest.raises(sc5.Sepconv5Error) as e:
+            sc5.tune_load(write("Another GPU", [entry(0, 0, th1, tw1, st1, 1)]))
+        assert e.value.status == sc5.ENOTFOUND
+        assert not sc5.tune_lookup("f32", "f32", 64, 64)[1]
+    finally:
+        sc5.autotune(0, [])
+    assert not sc5.tune_lookup("f32", "f32", 256, 256)[1]
