@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "sc5_internal.h"
+#include "sc5_serve_host.h"
 
 namespace sc5 {
 
@@ -40,64 +41,9 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr size_t kAlign = 256;
 constexpr int kSlots = 8;                       // descriptor slots (launches in flight)
 constexpr size_t kSlotBytes = 8u << 20;         // descriptors + tile list per launch
 constexpr int kMaxQueued = 1 << 16;             // pending requests before back-pressure
-
-size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-// First-fit allocator over [0, size) with coalescing of free blocks.
-class Arena {
-public:
-    void reset(size_t size)
-    {
-        free_.clear();
-        free_[0] = size;
-        used_ = 0;
-        size_ = size;
-    }
-    bool alloc(size_t n, size_t *off)
-    {
-        n = round_up(n, kAlign);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= n) {
-                *off = it->first;
-                const size_t rest = it->second - n;
-                const size_t start = it->first + n;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                used_ += n;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t n)
-    {
-        n = round_up(n, kAlign);
-        used_ -= n;
-        auto it = free_.emplace(off, n).first;
-        auto next = std::next(it);
-        if (next != free_.end() && it->first + it->second == next->first) {
-            it->second += next->second;
-            free_.erase(next);
-        }
-        if (it != free_.begin()) {
-            auto prev = std::prev(it);
-            if (prev->first + prev->second == it->first) {
-                prev->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-    size_t size() const { return size_; }
-
-private:
-    std::map<size_t, size_t> free_;
-    size_t used_ = 0, size_ = 0;
-};
 
 struct Request {
     uint64_t id = 0;
@@ -108,38 +54,6 @@ struct Request {
     cudaEvent_t h2d = nullptr;
     bool done = false;
     sc5_status status = SC5_OK;
-};
-
-// Phase durations of the last kPhaseLog completed requests (a ring).
-struct PhaseLog {
-    static constexpr size_t kPhaseLog = size_t(1) << 20;
-    std::vector<float> q, s, r;  // queue, stage, run (microseconds)
-    size_t n = 0;
-    static float us(Clock::duration d) { return std::chrono::duration<float, std::micro>(d).count(); }
-    void add(Clock::duration dq, Clock::duration ds, Clock::duration dr)
-    {
-        if (q.size() < kPhaseLog) {
-            q.push_back(us(dq));
-            s.push_back(us(ds));
-            r.push_back(us(dr));
-        } else {
-            const size_t i = n % kPhaseLog;
-            q[i] = us(dq);
-            s[i] = us(ds);
-            r[i] = us(dr);
-        }
-        ++n;
-    }
-    // p-th percentile (nearest rank) of a copy of v; 0 if empty.
-    static double pct(std::vector<float> v, double p)
-    {
-        if (v.empty()) return 0.0;
-        size_t k = static_cast<size_t>(std::ceil(p / 100.0 * v.size()));
-        k = k ? k - 1 : 0;
-        if (k >= v.size()) k = v.size() - 1;
-        std::nth_element(v.begin(), v.begin() + static_cast<std::ptrdiff_t>(k), v.end());
-        return v[k];
-    }
 };
 
 struct Launch {
@@ -204,8 +118,8 @@ struct sc5_server_s {
     size_t need_bytes(const sc5_image &im) const
     {
         const int es = dtype_bytes(cfg.dtype);
-        return round_up(static_cast<size_t>(cfg.planes) * im.H * im.in_pitch * es, kAlign) +
-               round_up(static_cast<size_t>(cfg.planes) * (im.H - 4) * im.out_pitch * es, kAlign);
+        return round_up(static_cast<size_t>(cfg.planes) * im.H * im.in_pitch * es, kArenaAlign) +
+               round_up(static_cast<size_t>(cfg.planes) * (im.H - 4) * im.out_pitch * es, kArenaAlign);
     }
 
     void scheduler_loop();
@@ -283,7 +197,7 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
         // upper bound on this image's share: descriptor + smallest-tile work-list
         const size_t tiles = static_cast<size_t>(cfg.planes) * ((r->img.H - 4 + 31) / 32) * ((r->img.W - 4 + 127) / 128);
         const size_t add = sizeof(ImgDesc) + tiles * sizeof(TileRec);
-        if (!group.empty() && bytes + add + kAlign > kSlotBytes) break;
+        if (!group.empty() && bytes + add + kArenaAlign > kSlotBytes) break;
         bytes += add;
         sc5_image d = r->img;
         d.in = arena_base + r->in_off;
