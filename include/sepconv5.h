@@ -428,8 +428,11 @@ SC5_API sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out);
  * and writes the W-4 output values of each row of `out` (its row padding is
  * left as it was) asynchronously, so both must stay valid until serve_poll
  * returns SC5_OK for the ticket (pinned memory gives the fastest copies).
- * Returns SC5_EAGAIN when the request could never fit the budget together
- * with what is queued (backpressure: retry later), SC5_EINVAL for bad shapes. */
+ * A request that fits the budget but not the arena's free space waits in the
+ * queue until earlier requests retire.  Returns SC5_EAGAIN when 65536
+ * requests are already queued (back-pressure: retry later), SC5_EINVAL for a
+ * bad shape, non-finite taps, a scale that is not finite and > 0, or a
+ * request that needs more than the whole budget. */
 SC5_API sc5_status serve_submit(sc5_server srv, const sc5_image *req, uint64_t *ticket);
 
 /* Wait up to timeout_us (0 = just test, <0 = forever) for a ticket.  SC5_OK:

@@ -141,6 +141,12 @@ def test_refusals(sc5):
     bad["in_pitch"] = 66  # 132 bytes: not a multiple of 16
     with pytest.raises(sc5.Sepconv5Error):
         srv.submit(bad)
+    for key, value in (("k", [0.2, float("nan"), 0.2, 0.2, 0.2]), ("in_scale", float("inf")), ("out_scale", 0.0)):
+        r, _ = _request(2, 64, 64, "bf16")
+        r[key] = value
+        with pytest.raises(sc5.Sepconv5Error) as e:
+            srv.submit(r)
+        assert e.value.status == sc5.EINVAL, key
     with pytest.raises(sc5.Sepconv5Error) as e:
         srv.poll(123456, 0)
     assert e.value.status == sc5.ENOTFOUND
