@@ -113,3 +113,35 @@ def test_tune_table_load_and_lookup(sc5, tmp_path):
     finally:
         sc5.autotune(0, [])
     assert not sc5.tune_lookup("f32", "f32", 256, 256)[1]
+
+
+def test_binding_structs_match_header(tmp_path):
+    """The binding's ctypes structures have the header's field names, offsets
+    and sizes: a C program compiled against include/sepconv5.h prints
+    offsetof/sizeof for every field the binding declares."""
+    import ctypes
+    import subprocess
+    from paper_1711_09791_gb300 import sepconv5
+    structs = {"sc5_plan_desc": sepconv5.PlanDesc, "sc5_image": sepconv5.Image,
+               "sc5_pyramid_desc": sepconv5.PyramidDesc, "sc5_serve_cfg": sepconv5.ServeCfg,
+               "sc5_serve_stats": sepconv5.ServeStats}
+    rename = {"in_": "in"}  # a Python keyword in the binding
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sepconv5.h"', "int main(void) {"]
+    expect = []
+    for cname, py in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            lines.append(f'printf("%zu %zu\\n", offsetof({cname}, {rename.get(fname, fname)}), '
+                         f'sizeof((({cname} *)0)->{rename.get(fname, fname)}));')
+            f = getattr(py, fname)
+            expect.append((f.offset, f.size))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                           str(src)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = [int(x) if " " not in x else tuple(int(v) for v in x.split()) for x in out if x]
+    assert got == expect
