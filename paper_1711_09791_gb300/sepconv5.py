@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
         "sepconv5_run_inplace": [V, V, POINTER(c_float), c_float, V],
         "sepconv5_hpass": [V, V, V, c_int64, POINTER(c_float), V],
         "sepconv5_vpass": [V, V, c_int64, V, POINTER(c_float), c_float, c_float, V],
+        "sepconv5_two_pass_noalloc": [V, V, c_int32, c_int32, c_int32, c_int64, c_int64, c_int32, c_int32,
+                                      POINTER(c_float), c_float, c_float, V],
         "sepconv5_device_status": [V, POINTER(c_int32)],
         "sepconv5_run_batch": [V, c_int32, POINTER(Image), V],
         "sepconv5_batch_create": [V, c_int32, POINTER(Image), POINTER(V)],

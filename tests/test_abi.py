@@ -145,3 +145,36 @@ def test_binding_structs_match_header(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = [int(x) if " " not in x else tuple(int(v) for v in x.split()) for x in out if x]
     assert got == expect
+
+
+def _c_param_kind(param: str) -> str:
+    import re
+    p = re.sub(r"\bconst\b", "", param).strip()
+    if "*" in p or "[" in p or re.match(r"(sc5_plan|sc5_batch|sc5_server|sc5_pyramid)\b", p):
+        return "ptr"
+    base = p.split()[0]
+    return {"int32_t": "i32", "int": "i32", "int64_t": "i64", "uint64_t": "u64", "float": "f32",
+            "double": "f64", "size_t": "size"}[base]
+
+
+def test_binding_signatures_match_header(sc5):
+    """Every function the header declares is bound with the same number of
+    parameters, each of the same kind (pointer, 32/64-bit integer, float,
+    double), and returns a 32-bit status."""
+    import ctypes
+    import re
+    text = open(sc5.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"^SC5_API\s+([\w\s\*]+?)\b((?:sepconv5|serve)_\w+)\s*\(([^)]*)\)\s*;", text, re.M)
+    assert len(protos) == len(sc5.header_symbols())
+    lib = sc5.load()
+    kinds = {ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_uint64: "u64", ctypes.c_float: "f32",
+             ctypes.c_double: "f64", ctypes.c_void_p: "ptr", ctypes.c_char_p: "ptr"}
+    for ret, name, params in protos:
+        params = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        want = [_c_param_kind(p) for p in params]
+        f = getattr(lib, name)
+        got = [kinds.get(a, "ptr" if issubclass(a, ctypes._Pointer) else "?") for a in (f.argtypes or [])]
+        assert got == want, (name, got, want)
+        if "sc5_status" in ret:
+            assert f.restype is ctypes.c_int32, name
