@@ -159,7 +159,7 @@ __device__ __forceinline__ void hwc_strip(const TIn *__restrict__ s, const uint6
 }
 
 // Per-image parameters of the HWC kernel.
-struct alignas(64) HwcDesc {
+struct alignas(128) HwcDesc {  // CUtensorMap's own alignment
     CUtensorMap tmap;   // 2-D: (3*W values, H rows)
     void *out;          // first VALID output value
     int64_t out_pitch;  // elements

@@ -22,7 +22,7 @@ constexpr int kDevErrTmaTimeout = 1;
 
 // Per-image description read by the fused kernels.  The tensor map describes
 // the input image as a 3-D tensor (x = column, y = row, z = plane).
-struct alignas(64) ImgDesc {
+struct alignas(128) ImgDesc {  // CUtensorMap's own alignment
     CUtensorMap tmap;      // 128 bytes
     void *out;             // first VALID output pixel (plane 0)
     int64_t out_pitch;     // elements
@@ -35,7 +35,7 @@ struct alignas(64) ImgDesc {
     float K[kTaps * kTaps];  // direct form: the 5x5 matrix, row-major, K[i][j] at offset (i-2, j-2)
     int32_t pad_[8];
 };
-static_assert(sizeof(ImgDesc) % 64 == 0, "ImgDesc must keep the tensor map 64-byte aligned");
+static_assert(sizeof(ImgDesc) == 384, "ImgDesc: 128-byte tensor map + 216 bytes of parameters, padded to 128");
 
 // One entry of a batch work-list: a (th x tw) output tile of one plane.
 struct TileRec {
