@@ -92,7 +92,6 @@ struct sc5_server_s {
     uint64_t next_id = 1;
     int admitted = 0;
     bool stop = false;
-    sc5_status fatal = SC5_OK;
     sc5_serve_stats stats{};
     std::thread sched, compl_;
     int next_stream = 0;
