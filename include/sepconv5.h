@@ -66,7 +66,7 @@ typedef enum {
     SC5_EINVAL = 1,     /* bad argument: sizes, alignment, null pointer, dtype/algo not built */
     SC5_ENOMEM = 2,     /* device or host allocation failed */
     SC5_ECUDA = 3,      /* a CUDA runtime/driver call failed */
-    SC5_EAGAIN = 4,     /* serve_submit: over budget or queue full; serve_poll: not done yet */
+    SC5_EAGAIN = 4,     /* serve_submit: queue full (back-pressure); serve_poll: not done yet */
     SC5_ETIMEDOUT = 5,  /* serve_poll: timeout expired before completion */
     SC5_ENOTFOUND = 6,  /* unknown ticket / no tuning entry */
     SC5_EDEVICE = 7     /* a kernel reported a device-side error (a bounded wait ran out) */
@@ -124,9 +124,9 @@ typedef enum {
  * header reads n: k holds n values, tap t acts at offset t-(n-1)/2, the
  * VALID output is (H-n+1) x (W-n+1), the KEEP frame is (n-1)/2 pixels wide,
  * and H, W >= n.  Batches, serving, the two-pass and direct forms, the
- * offload and in-place calls are built for width 5.  tile_h/tile_w/stages: 0 = take the autotuned (or
- * built-in default) choice; otherwise one of the compiled fused-kernel shapes
- * (sepconv5_fused_configs).
+ * offload and in-place calls are built for width 5.
+ * tile_h/tile_w/stages: 0 = take the autotuned (or built-in default) choice;
+ * otherwise one of the compiled fused-kernel shapes (sepconv5_fused_configs).
  * Plane strides: 0 = planes stacked ([planes][H][pitch]: H*in_pitch for the
  * input, Hout*out_pitch for the output).  Any other value places plane p at
  * p*stride; the planes may then be stacked (stride >= H*pitch) or
@@ -192,8 +192,9 @@ SC5_API sc5_status sepconv5_plan_info(sc5_plan plan, int32_t *tile_h, int32_t *t
 
 /* Run the plan on one image: in (dev, in_dtype, [planes][H][in_pitch]),
  * out (dev, out_dtype, layout per border), k (host, the plan's taps values --
- * 5 unless the plan says otherwise -- copied by value).  in_scale > 0 and out_scale > 0 must be finite; the result code is
- * round(B * out_scale) with B computed from value(in)/in_scale.  `in` and
+ * 5 unless the plan says otherwise -- copied by value).  in_scale and
+ * out_scale must be finite and > 0; the result code is round(B * out_scale)
+ * with B computed from value(in)/in_scale.  `in` and
  * `out` must not overlap.  Asynchronous on `stream`. */
 SC5_API sc5_status sepconv5_run(sc5_plan plan, const void *in, void *out, const float k[5],
                         float in_scale, float out_scale, void *stream);
@@ -359,8 +360,9 @@ SC5_API sc5_status sepconv5_fused_configs(int32_t in_dtype, int32_t out_dtype, i
  * below 2^14 to 2^24 pixels and above), dtype pair in `dtypes` (pairs in, out)
  * and kernel kind (the single-image kernel of plans; the work-list kernel of
  * batches and merged serving launches), time every compiled shape and CTA
- * count on synthetic images on the current device and keep the fastest.  mode: 0 = off (built-in defaults), 1 = quick (one size
- * per class), 2 = full.  The table is kept in the process and, if path is
+ * count on synthetic images on the current device and keep the fastest.
+ * mode: 0 = off (clears the table: built-in defaults), 1 = quick (3
+ * repetitions per configuration), 2 = full (10 repetitions).  The table is kept in the process and, if path is
  * not NULL, written there as JSON keyed by GPU name.  Allocates device memory
  * for its test images. */
 SC5_API sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int32_t n_pairs,
