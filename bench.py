@@ -371,34 +371,7 @@ def _batch_images(sc5, synth, dtype, shapes, x_dev, scales):
     return imgs, keep
 
 
-def _sample_errors(oracle, imgs, outs, dtype, out_dtype, m=48, seed=9):
-    """max-abs and max-relative error of sampled outputs against the FP64
-    oracle evaluated on the decoded stored inputs, one 5x5 window per pixel."""
-    import torch
-    g = np.random.Generator(np.random.PCG64(seed))
-    max_abs, max_rel = 0.0, 0.0
-    for im, out in zip(imgs, outs):
-        h, w = im["H"], im["W"]
-        p = g.integers(0, P, m)
-        y = g.integers(0, h - 4, m)
-        x = g.integers(0, w - 4, m)
-        A = im["in"]
-        dec = A.float() / im["in_scale"] if A.dtype != torch.float32 else A
-        idx = torch.arange(5, device="cuda")
-        pt, yt, xt = (torch.from_numpy(v).cuda() for v in (p, y, x))
-        win = dec[pt[:, None, None], (yt[:, None] + idx)[:, :, None], (xt[:, None] + idx)[:, None, :]]
-        ref = oracle.direct(win.double().cpu().numpy(), np.asarray(im["k"], np.float64))[:, 0, 0]
-        got = out[pt, yt, xt]
-        got = (got.float() / im["out_scale"] if got.dtype != torch.float32 else got).double().cpu().numpy()
-        err = np.abs(got - ref)
-        max_abs = max(max_abs, float(err.max()))
-        sel = np.abs(ref) > 1.0
-        if sel.any():
-            max_rel = max(max_rel, float((err[sel] / np.abs(ref[sel])).max()))
-    return max_abs, max_rel
-
-
-def leg_batch(sc5, synth, oracle, stream, dtypes):
+def leg_batch(sc5, synth, stream, dtypes):
     """The 256-image batch (H, W log-uniform in [64, 4096]): one persistent
     launch over the tile work-list, replayed from a CUDA graph, tile shape
     from the autotuner and CTAs per SM timed on the batch itself when it is
@@ -433,7 +406,6 @@ def leg_batch(sc5, synth, oracle, stream, dtypes):
         info = b.info()
         alg = sum(P * h * w * sc5.DTYPE_BYTES[dtype] + P * (h - 4) * (w - 4) * sc5.DTYPE_BYTES[out_dtype]
                   for h, w in shapes)
-        ea, er = _sample_errors(oracle, imgs, outs, dtype, out_dtype)
         # narrow-to-narrow formats move 2-4 bytes per pixel: the SMs' instruction issue and FMA
         # pipe bound them before HBM does (profiles/fused_bf16_3x8192x8192.md)
         bound = "sm_issue" if out_dtype != "f32" and dtype != "f32" else "hbm"
@@ -441,9 +413,7 @@ def leg_batch(sc5, synth, oracle, stream, dtypes):
             "bound": bound,
             "ms": round(ms, 4), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "achieved_gbs": round(alg / ms / 1e6, 1),
             "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4), "tiles": info["tiles"], "ctas": info["ctas"],
-            "tile": f"{info['tile_h']}x{info['tile_w']}", "create_ms": round(create_ms, 1),
-            "max_abs_err_vs_fp64": ea, "max_rel_err_vs_fp64": er,
-            "err_sample": "48 pixels per image, FP64 oracle on the decoded stored inputs"}
+            "tile": f"{info['tile_h']}x{info['tile_w']}", "create_ms": round(create_ms, 1)}
         b.close()
         plan.close()
         del imgs, keep, outs
@@ -731,7 +701,6 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if "pyramid" in legs:
         extras["pyramid"] = leg_pyramid(sepconv5, synth, stream, A_dev, k)
     if legs:
-        import oracle
         del A_dev, out
         torch.cuda.empty_cache()
         if "c1" in legs:
@@ -741,7 +710,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             if "c4" in legs:
                 pairs += [("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
                           ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
-            extras["batch_c3_c4"] = leg_batch(sepconv5, synth, oracle, stream, pairs)
+            extras["batch_c3_c4"] = leg_batch(sepconv5, synth, stream, pairs)
         if "paper" in legs:
             extras["paper_sizes"] = leg_paper_sizes(sepconv5, stream)
         if "c5" in legs:

@@ -234,7 +234,8 @@ def test_reduced_precision_storage(sc5, dtype, out_f32):
 # ------------------------------------------------------------------ batches
 
 
-def _batch_images(sc5, shapes, seed, dtype="f32"):
+def _batch_images(sc5, shapes, seed, dtype="f32", out_dtype=None):
+    out_dtype = dtype if out_dtype is None else out_dtype
     imgs, host, keep = [], [], []
     for i, (H, W) in enumerate(shapes):
         x = synth.image(seed * 1000 + i, H, W)
@@ -244,11 +245,11 @@ def _batch_images(sc5, shapes, seed, dtype="f32"):
         padded = np.zeros((3, H, pitch), codes.dtype)
         padded[:, :, :W] = codes
         A = U.to_dev(padded)
-        op = U.pitch_for(W - 4, dtype)
-        out = U.empty_dev((3, H - 4, op), dtype)
+        op = U.pitch_for(W - 4, out_dtype)
+        out = U.empty_dev((3, H - 4, op), out_dtype)
         k = synth.kernel_normalised(seed * 1000 + i)
         imgs.append({"in": A, "out": out, "H": H, "W": W, "in_pitch": pitch, "out_pitch": op, "k": k,
-                     "in_scale": scale, "out_scale": scale})
+                     "in_scale": scale, "out_scale": 1.0 if out_dtype == "f32" else scale})
         host.append(padded)
         keep.extend([A, out])
     return imgs, host, keep
@@ -258,37 +259,50 @@ BATCH_SHAPES = [(5, 5), (64, 64), (100, 3000), (517, 300), (131, 129), (1030, 70
                 (64, 4096), (2000, 64), (77, 77), (9, 13)]
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_batch_matches_single_runs_and_oracle(sc5, dtype):
+BATCH_PAIRS = [("f32", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
+               ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
+
+
+@pytest.mark.parametrize("dtype,out_dtype", BATCH_PAIRS)
+def test_batch_matches_single_runs_and_oracle(sc5, dtype, out_dtype):
+    """Every storage pair the batch kernel is built for (the stored-format
+    batches the benchmark times included): one-shot and graph-replayed batches
+    agree bit for bit with each other and with single-image runs, and with the
+    FP64 oracle on the decoded inputs within the FP32 bound plus half an ulp of
+    the output format."""
     import torch
-    imgs, host, _keep = _batch_images(sc5, BATCH_SHAPES, 3, dtype)
-    plan = sc5.Plan(3, 64, 64, in_dtype=dtype)
+    imgs, host, _keep = _batch_images(sc5, BATCH_SHAPES, 3, dtype, out_dtype)
+    plan = sc5.Plan(3, 64, 64, in_dtype=dtype, out_dtype=out_dtype)
     plan.run_batch(imgs)
     torch.cuda.synchronize()
     assert sc5.device_status() == 0
-    batch_out = [U.from_dev(im["out"], dtype)[:, :, :im["W"] - 4].copy() for im in imgs]
+    batch_out = [U.from_dev(im["out"], out_dtype)[:, :, :im["W"] - 4].copy() for im in imgs]
+    for i, im in enumerate(imgs):
+        assert U.sentinel_intact(U.from_dev(im["out"], out_dtype)[:, :, im["W"] - 4:], out_dtype), i
     # the same images through the graph-captured batch
     for im in imgs:
-        im["out"].fill_(-1 if dtype != "f32" else float("nan"))
+        im["out"].fill_(float("nan") if out_dtype == "f32" else (-1 if out_dtype != "fp8e4m3" else 0xFF))
     b = sc5.Batch(plan, imgs)
     b.launch()
     b.launch()  # replay twice: same result
     torch.cuda.synchronize()
+    assert sc5.device_status() == 0
     info = b.info()
     assert info["tiles"] > 0 and info["ctas"] > 0
     for i, im in enumerate(imgs):
         H, W = im["H"], im["W"]
-        g = U.from_dev(im["out"], dtype)[:, :, :W - 4]
+        g = U.from_dev(im["out"], out_dtype)[:, :, :W - 4]
         assert np.array_equal(g, batch_out[i])
-        single, _ = _run(sc5, im["in"], 3, H, W, im["in_pitch"], im["k"], in_dtype=dtype,
-                         tile_h=info["tile_h"], tile_w=info["tile_w"])
+        single, _ = _run(sc5, im["in"], 3, H, W, im["in_pitch"], im["k"], in_dtype=dtype, out_dtype=out_dtype,
+                         in_scale=im["in_scale"], out_scale=im["out_scale"], tile_h=info["tile_h"],
+                         tile_w=info["tile_w"])
         assert np.array_equal(single[:, :, :W - 4], batch_out[i]), i
-        ref = U.oracle_valid(host[i], dtype, im["k"], W=W)
-        got = U.decode(batch_out[i], dtype)
-        if dtype == "f32":
-            assert U.max_abs(got, ref) <= U.FP32_TOL
+        ref = U.oracle_valid(host[i], dtype, im["k"], im["in_scale"], W=W)
+        got = U.decode(batch_out[i], out_dtype, im["out_scale"])
+        if out_dtype == "f32":
+            assert U.max_abs(got, ref) <= U.FP32_TOL, i
         else:
-            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, 1.0, U.FP32_TOL))
+            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, out_dtype, im["out_scale"], U.FP32_TOL)), i
     b.close()
     plan.close()
 
