@@ -116,3 +116,45 @@ def test_reference_arm_line():
     assert d["config"] == bench.run_config(1)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_oracle_is_test_infrastructure_only():
+    """Static check of the oracle's isolation: no file of the product package
+    (Python or CUDA/C++) names the oracle module or its C source, the oracle
+    names nothing of the package's arithmetic (only the seeded generators are
+    shared, through the tests), and bench.py imports it only in its two CPU
+    baseline functions."""
+    import ast
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1711_09791_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                continue
+            text = open(os.path.join(dirpath, f)).read()
+            if f.endswith(".py"):
+                tree = ast.parse(text)
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        assert all(a.name.split(".")[0] != "oracle" for a in node.names), f
+                    if isinstance(node, ast.ImportFrom):
+                        assert (node.module or "").split(".")[0] != "oracle", f
+            else:
+                assert "sepconv5_oracle" not in text and "sc5o_" not in text, f
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith((".py", ".c")):
+            text = open(os.path.join(root, "oracle", f)).read()
+            assert "import paper_1711_09791_gb300" not in text and "from paper_1711_09791_gb300" not in text, f
+            assert "sepconv5.h" not in text and "sc5_internal" not in text, f
+    tree = ast.parse(open(os.path.join(root, "bench.py")).read())
+    users = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.Import) and any(a.name == "oracle" for a in node.names):
+                    users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any(isinstance(n, ast.Import) and any(a.name == "oracle" for a in n.names) for n in top)
+    assert users == {"oracle_sample", "run_reference"}, users
