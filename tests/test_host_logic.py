@@ -158,3 +158,30 @@ def test_oracle_is_test_infrastructure_only():
     top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
     assert not any(isinstance(n, ast.Import) and any(a.name == "oracle" for a in n.names) for n in top)
     assert users == {"oracle_sample", "run_reference"}, users
+
+
+def test_device_waits_are_bounded_and_nothing_traps():
+    """Static check of the failure-detection design: every mbarrier wait in
+    the kernels goes through the bounded helper (global-timer limit, then an
+    error status), the raw try-wait appears nowhere else, and no kernel traps
+    or asserts."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_1711_09791_gb300", "csrc")
+    raw_waits = {}
+    for f in sorted(os.listdir(csrc)):
+        if not f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            continue
+        text = open(os.path.join(csrc, f)).read()
+        assert "__trap" not in text and not re.search(r"asm[^;]*\btrap\b", text), f
+        assert not re.search(r"(?<!static_)\bassert\s*\(", text), f
+        assert text.count("mbarrier.try_wait") + text.count("mbarrier.test_wait") == (1 if f == "sc5_device.cuh" else 0), f
+        n = len(re.findall(r"\bmbar_try_wait\s*\(", text))
+        if n:
+            raw_waits[f] = n
+    # the definition and the two calls inside mbar_wait_bounded
+    assert raw_waits == {"sc5_device.cuh": 3}, raw_waits
+    dev = open(os.path.join(csrc, "sc5_device.cuh")).read()
+    body = dev[dev.index("bool mbar_wait_bounded("):]
+    body = body[:body.index("\n}\n")]
+    assert "global_timer_ns()" in body and "return false" in body
