@@ -366,10 +366,10 @@ extern "C" sc5_status serve_submit(sc5_server srv, const sc5_image *req, uint64_
     const sc5_image &im = *req;
     const int es = dtype_bytes(srv->cfg.dtype);
     if (!im.in || !im.out) return fail(SC5_EINVAL, "null image pointer");
-    if (im.H < 5 || im.W < 5 || im.H > 65535 * 8 || im.in_pitch < im.W || im.out_pitch < im.W - 4 ||
-        (im.in_pitch * es) % 16)
-        return fail(SC5_EINVAL, "bad shape: 5 <= H <= 524280, W >= 5, in_pitch >= W with in_pitch * element size "
-                                "a multiple of 16, out_pitch >= W-4");
+    if (im.H < 5 || im.W < 5 || im.H > 65535 * 8 || im.W > (1 << 30) || im.in_pitch < im.W ||
+        im.out_pitch < im.W - 4 || (im.in_pitch * es) % 16)
+        return fail(SC5_EINVAL, "bad shape: 5 <= H <= 524280, 5 <= W <= 2^30, in_pitch >= W with in_pitch * "
+                                "element size a multiple of 16, out_pitch >= W-4");
     if (!(im.in_scale > 0.f) || !std::isfinite(im.in_scale) || !(im.out_scale > 0.f) || !std::isfinite(im.out_scale))
         return fail(SC5_EINVAL, "scales must be finite and > 0");
     for (float t : im.k)
