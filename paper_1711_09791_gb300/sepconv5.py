@@ -176,11 +176,12 @@ class Plan:
                  in_dtype="f32", out_dtype=None, border="valid", algo="fused", tile_h=0, tile_w=0, stages=0,
                  ctas_per_sm=0, in_plane_stride=0, out_plane_stride=0, taps=5, layout="planar"):
         out_dtype = in_dtype if out_dtype is None else out_dtype
+        taps = taps or 5  # 0 selects the default width, as in the C descriptor
         b = BORDERS[border] if isinstance(border, str) else int(border)
         d = PlanDesc()
         d.planes, d.H, d.W = planes, H, W
         d.in_pitch = W if in_pitch is None else in_pitch
-        d.out_pitch = (W if b == 1 else W - 4) if out_pitch is None else out_pitch
+        d.out_pitch = (W if b == 1 else W - (taps - 1)) if out_pitch is None else out_pitch
         d.in_dtype, d.out_dtype = _dt(in_dtype), _dt(out_dtype)
         d.border = b
         d.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
@@ -189,9 +190,6 @@ class Plan:
         d.taps = taps
         d.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
         self.taps = taps
-        halo = taps - 1
-        if out_pitch is None:
-            d.out_pitch = W if b == 1 else W - halo
         self.desc = d
         h = c_void_p()
         _check(load().sepconv5_plan(byref(d), byref(h)), "sepconv5_plan")
@@ -239,7 +237,7 @@ class Plan:
 
     def run_batch(self, images, stream=None):
         arr = make_images(images)
-        _check(load().sepconv5_run_batch(self._h, len(images), arr, _stream(stream)), "sepconv5_run_batch")
+        _check(load().sepconv5_run_batch(self._h, len(arr), arr, _stream(stream)), "sepconv5_run_batch")
 
     def close(self):
         if getattr(self, "_h", None):
