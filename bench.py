@@ -10,6 +10,10 @@ on the same image, the end-to-end offload call with host buffers
 oracle timed on a bounded sample (rank 0, one GPU only).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --case dtype=bf16,out=bf16,tile=128x128x2 --steps 5 --warmup 3
+
+The second form times one configuration on its own and prints its JSON line
+(the command the ncu summaries under profiles/ were taken with).
 
 Multi-GPU (launched by torchrun): every rank convolves its own image (no
 collective on the data path; weak scaling); the time is the max over ranks.
@@ -51,6 +55,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="only the timed fused leg")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests per offered load")
     ap.add_argument("--legs", default="c1,c3,c4,paper,pyramid,c5", help="extra configs to run beside the headline")
+    ap.add_argument("--case", default=None,
+                    help="time one configuration instead of the contract run (the command the ncu captures use): "
+                         "comma-separated key=value with keys dtype, out, algo (fused|two_pass|direct|reduce), "
+                         "layout (planar|hwc), planes, H, W, tile (THxTWxSTAGES), ctas; --steps timed launches "
+                         "after --warmup")
     return ap.parse_args()
 
 
@@ -113,36 +122,51 @@ def profiled_traffic() -> int | None:
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons, each stamped with
+    the host time at which it arrived.  start() returns once the first sample
+    is in (or after a few seconds without one), so that sampling already runs
+    when the warm-up begins; stop() reports the samples of the window that
+    mark() opened and closed, plus the first sample after it, because a timed
+    region of a few milliseconds can fall between two samples."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 10
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
         self.t = None
+        self.first = threading.Event()
+        self.window = [None, None]
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        self.first.wait(wait_s)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+            self.first.set()
+
+    def mark(self, which: int):
+        """0: the window opens (before the warm-up); 1: it closes (after the timed steps)."""
+        self.window[which] = time.perf_counter()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(3 * self.PERIOD_MS / 1e3)  # let the first sample after the window arrive
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -150,9 +174,13 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
+        t0 = self.window[0] if self.window[0] is not None else float("-inf")
+        t1 = self.window[1] if self.window[1] is not None else float("inf")
+        inside = [ln for ts, ln in self.lines if t0 <= ts <= t1]
+        after = [ln for ts, ln in self.lines if ts > t1][:1]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside + after:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -166,9 +194,10 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        # median of the samples taken while the warm-up and timed steps ran
+        # median over the warm-up and timed steps (and the first sample after them)
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_window": len(inside), "period_ms": self.PERIOD_MS,
+                "window": "warm-up and timed steps of the headline, plus the next sample"}
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -407,7 +436,7 @@ def leg_batch(sc5, synth, stream, dtypes):
         alg = sum(P * h * w * sc5.DTYPE_BYTES[dtype] + P * (h - 4) * (w - 4) * sc5.DTYPE_BYTES[out_dtype]
                   for h, w in shapes)
         # narrow-to-narrow formats move 2-4 bytes per pixel: the SMs' instruction issue and FMA
-        # pipe bound them before HBM does (profiles/fused_bf16_3x8192x8192.md)
+        # pipe bound them before HBM does
         bound = "sm_issue" if out_dtype != "f32" and dtype != "f32" else "hbm"
         results[f"{dtype}->{out_dtype}"] = {
             "bound": bound,
@@ -525,6 +554,80 @@ def leg_serve(sc5, synth, n_req):
     return out
 
 
+# ------------------------------------------------------------------ one configuration
+
+
+def parse_case(spec: str) -> dict:
+    """`--case` key=value list -> options (defaults: 3 x 8192 x 8192 FP32 fused, planar)."""
+    c = {"dtype": "f32", "out": None, "algo": "fused", "layout": "planar", "planes": P, "H": H, "W": W,
+         "tile": "", "ctas": 0}
+    for item in filter(None, (x.strip() for x in spec.split(","))):
+        key, _, val = item.partition("=")
+        if key not in c:
+            raise SystemExit(f"--case: unknown key {key!r} (keys: {', '.join(c)})")
+        c[key] = int(val) if key in ("planes", "H", "W", "ctas") else val
+    c["out"] = c["out"] or c["dtype"]
+    return c
+
+
+def run_case(args):
+    """One configuration on a synthetic image (pixels uniform in [0, 255) drawn
+    on the device, seed 2; k as the headline; FP8 inputs scaled by 448/max):
+    median CUDA-event time of --steps launches after --warmup, and the
+    algorithmic GB/s (input read once, output written once)."""
+    import torch
+
+    from paper_1711_09791_gb300 import sepconv5 as sc5
+    from paper_1711_09791_gb300 import synth
+    c = parse_case(args.case)
+    sc5.load()
+    Pc, Hc, Wc, dt, odt = c["planes"], c["H"], c["W"], c["dtype"], c["out"]
+    es, eo = sc5.DTYPE_BYTES[dt], sc5.DTYPE_BYTES[odt]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}
+    g = torch.Generator(device="cuda").manual_seed(2)
+    x = torch.rand((Pc, Hc, Wc), generator=g, device="cuda") * 255.0
+    scale = 448.0 / float(x.max()) if dt == "fp8e4m3" else 1.0
+    th = tw = st = 0
+    if c["tile"]:
+        th, tw, st = (int(v) for v in c["tile"].split("x"))
+    Ho, Wo = sc5.reduce_dims(Hc, Wc) if c["algo"] == "reduce" else (Hc - 4, Wc - 4)
+    if c["layout"] == "hwc":
+        pitch = -(-3 * Wc * es // 16) * 16 // es
+        opitch = -(-3 * Wo // 4) * 4
+        A = torch.zeros((Hc, pitch), dtype=tdt[dt], device="cuda")
+        A[:, :3 * Wc] = (x * scale).permute(1, 2, 0).reshape(Hc, 3 * Wc).to(tdt[dt])
+        out = torch.empty((Ho, opitch), dtype=tdt[odt], device="cuda")
+    else:
+        pitch = -(-Wc * es // 16) * 16 // es
+        opitch = -(-Wo * eo // 16) * 16 // eo
+        A = torch.zeros((Pc, Hc, pitch), dtype=tdt[dt], device="cuda")
+        A[:, :, :Wc] = (x * scale).to(tdt[dt])
+        out = torch.empty((Pc, Ho, opitch), dtype=tdt[odt], device="cuda")
+    del x
+    plan = sc5.Plan(Pc, Hc, Wc, pitch, opitch, dt, odt, "valid", c["algo"], th, tw, st, c["ctas"], layout=c["layout"])
+    k = synth.kernel_normalised(SEED)
+    out_scale = scale if odt == "fp8e4m3" else 1.0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 0)):
+        plan.run(A, out, k, scale, out_scale, stream=stream)
+    times = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(args.steps, 1)):
+        e0.record(stream)
+        plan.run(A, out, k, scale, out_scale, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if sc5.device_status(stream) != 0:
+        raise SystemExit("a kernel reported a device error")
+    info = plan.info()
+    plan.close()
+    ms = statistics.median(times)
+    alg = Pc * Hc * Wc * es + Pc * Ho * Wo * eo
+    return {"case": c, "ms": round(ms, 5), "gbs": round(alg / ms / 1e6, 1), "mpix_s": round(Hc * Wc / ms / 1e3, 1),
+            "algorithmic_bytes": alg, "plan": info, "launches": len(times)}
+
+
 # ------------------------------------------------------------------ main legs
 
 
@@ -573,7 +676,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     smi_index = vis[local_rank] if local_rank < len(vis) and vis[local_rank].isdigit() else str(local_rank)
     sampler = ClockSampler(smi_index)
     sampler.start()
+    sampler.mark(0)
     ms, launches = timed(lambda: plan.run(A_dev, out, k, stream=stream), args.steps, max(args.warmup, 3))
+    sampler.mark(1)
     clocks = sampler.stop()
     if sepconv5.device_status(stream) != 0:
         raise RuntimeError("a kernel reported a device error during the timed region")
@@ -657,7 +762,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # end to end: host buffers through sepconv5_run_host
     A_host = torch.from_numpy(A).pin_memory()
     out_host = torch.empty((P, H - 4, W - 4), dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(args.steps // 50, 30))
+    e2e_steps = max(10, min(args.steps // 50, 30))
     for _ in range(2):
         plan.run_host(A_host, out_host, k, stream=stream)
     barrier()
@@ -773,6 +878,9 @@ def run_reference(args, rank: int, world: int):
 
 def main():
     args = parse()
+    if args.case is not None:
+        print(json.dumps(run_case(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

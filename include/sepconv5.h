@@ -260,8 +260,11 @@ SC5_API sc5_status sepconv5_vpass(sc5_plan plan, const float *T, int64_t t_pitch
  *   - planes * H * round_up(W-4, 4) must not exceed SC5_NOALLOC_MAX_T_FLOATS
  *     (e.g. 3 planes of 1152 x 1152), else SC5_EINVAL with a message; H <= 65535;
  *   - the first call on a device looks the array's device address up
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture;
+ *     (cudaGetSymbolAddress, with that device current) and caches it for
+ *     the life of the process; make that first call before any stream
+ *     capture.  A device reset (cudaDeviceReset) invalidates the cached
+ *     address: a process that resets the device must not call this entry
+ *     point afterwards;
  *   - it calls no cudaMalloc, cudaFree or other allocating routine;
  *   - all calls share the one array and it keeps the last call's contents;
  *     nothing in it has to start at zero (each call writes every element it

@@ -4,7 +4,10 @@
  *                         shapes, a refused descriptor, the error message.
  *   abi_example gpu    -- convolve a 3 x 67 x 133 image with k = e_2 (the
  *                         identity tap) and check the result equals the
- *                         interior of the input exactly.
+ *                         interior of the input exactly: through a plan,
+ *                         one pyramid REDUCE step, and the serving calls
+ *                         (the output buffer is named at submission and
+ *                         holds the result once serve_poll returns OK).
  * Prints "OK" and exits 0 on success.
  */
 #include <stdio.h>
@@ -118,6 +121,64 @@ static int gpu_checks(void)
                 }
     sepconv5_pyramid_destroy(pyr);
     free(l);
+
+    /* serving: two requests of the same image in page-locked host memory */
+    float *hin = NULL, *hout[2] = {NULL, NULL};
+    if (cudaMallocHost((void **)&hin, n_in * sizeof(float)) != cudaSuccess) return 1;
+    for (int r = 0; r < 2; ++r)
+        if (cudaMallocHost((void **)&hout[r], n_out * sizeof(float)) != cudaSuccess) return 1;
+    memcpy(hin, a, n_in * sizeof(float));
+    sc5_serve_cfg sc;
+    memset(&sc, 0, sizeof sc);
+    sc.hbm_budget_bytes = (size_t)64 << 20;
+    sc.max_inflight = 4;
+    sc.dtype = SC5_F32;
+    sc.planes = P;
+    sc.n_streams = 1;
+    sc.max_merge = 8;
+    sc.merge = 1;
+    sc5_server srv = NULL;
+    if (serve_create(&sc, &srv) != SC5_OK) {
+        fprintf(stderr, "serve_create: %s\n", sepconv5_last_error());
+        return 1;
+    }
+    uint64_t tickets[2];
+    for (int r = 0; r < 2; ++r) {
+        sc5_image im;
+        memset(&im, 0, sizeof im);
+        im.in = hin;
+        im.out = hout[r];
+        im.H = H;
+        im.W = W;
+        im.in_pitch = pitch;
+        im.out_pitch = Wv;
+        memcpy(im.k, k, sizeof k);
+        im.in_scale = im.out_scale = 1.f;
+        if (serve_submit(srv, &im, &tickets[r]) != SC5_OK) {
+            fprintf(stderr, "serve_submit: %s\n", sepconv5_last_error());
+            return 1;
+        }
+    }
+    for (int r = 0; r < 2; ++r) {
+        double lat = 0.0;
+        if (serve_poll(srv, tickets[r], -1, &lat) != SC5_OK || !(lat > 0.0)) {
+            fprintf(stderr, "serve_poll: %s\n", sepconv5_last_error());
+            return 1;
+        }
+        for (int pl = 0; pl < P; ++pl)
+            for (int y = 0; y < Hv; ++y)
+                for (int x = 0; x < Wv; ++x)
+                    if (hout[r][((size_t)pl * Hv + y) * Wv + x] != a[((size_t)pl * H + y + 2) * pitch + x + 2]) {
+                        fprintf(stderr, "served mismatch at %d %d %d\n", pl, y, x);
+                        return 1;
+                    }
+    }
+    double lat = 0.0;
+    if (serve_poll(srv, tickets[0], 0, &lat) != SC5_ENOTFOUND) return 1; /* retired */
+    if (serve_destroy(srv) != SC5_OK) return 1;
+    cudaFreeHost(hin);
+    cudaFreeHost(hout[0]);
+    cudaFreeHost(hout[1]);
     cudaFree(dl);
     cudaFree(da);
     cudaFree(db);

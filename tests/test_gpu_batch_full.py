@@ -1,9 +1,24 @@
 """The 256-image batch at full size (H and W log-uniform in [64, 4096],
-about 241 Mpix x 3 planes), in the launch configuration the benchmark times:
-autotuned shape, one persistent launch replayed from a CUDA graph.  Sampled
-pixels of every image are checked against the FP64 oracle one by one (a 5x5
-window per pixel), in FP32 and in every stored format (fp8 with its per-image
-scale 448/max)."""
+about 241 Mpix x 3 planes) in the launch configuration the benchmark times:
+autotuned shape, CTAs per SM timed on the batch at creation, one persistent
+launch replayed from a CUDA graph.  Every output pixel of every image is
+compared with the FP64 oracle, for FP32 and for every stored-format pair
+(bf16, f16, fp8-e4m3 with its per-image scale 448/max; output in the stored
+format or FP32):
+
+  * against the oracle on the exactly decoded stored input (the kernel's own
+    error): FP32 output within max-abs 2e-4, stored output within half an
+    ulp of its format at the result plus that FP32 bound;
+  * against the oracle on the original FP32 image (the error the storage
+    format adds end to end): measured and reported, not bounded.
+
+With SC5_REPORT_DIR set, the measured errors are written there as
+error_batch.json (max-abs, max-abs / 255, and the largest relative error
+over pixels whose reference exceeds 1 in magnitude, per dtype pair).
+"""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -13,53 +28,122 @@ from tests import _util as U
 
 pytestmark = pytest.mark.gpu
 
+PAIRS = [("f32", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
+         ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]
+N_IMAGES = 256
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "fp8e4m3"])
-def test_full_batch_sampled(dtype):
+
+class ErrStats:
+    """Running max-abs and max-relative error of one comparison."""
+
+    def __init__(self):
+        self.max_abs = 0.0
+        self.max_rel = 0.0
+        self.pixels = 0
+
+    def add(self, got: np.ndarray, ref: np.ndarray):
+        d = np.abs(got - ref)
+        self.max_abs = max(self.max_abs, float(d.max()))
+        big = np.abs(ref) > 1.0
+        if big.any():
+            self.max_rel = max(self.max_rel, float((d[big] / np.abs(ref[big])).max()))
+        self.pixels += got.size
+
+    def report(self) -> dict:
+        return {"max_abs": self.max_abs, "max_abs_over_255": self.max_abs / 255.0,
+                "max_rel_where_abs_ref_gt_1": self.max_rel, "plane_pixels": self.pixels}
+
+
+def _torch_dtype(torch, dt):
+    return {"f32": torch.float32, "bf16": torch.int16, "f16": torch.int16, "fp8e4m3": torch.uint8}[dt]
+
+
+def _codes_view(a: np.ndarray) -> np.ndarray:
+    return a.view(np.int16) if a.dtype == np.uint16 else a
+
+
+@pytest.fixture(scope="module")
+def batch_outputs():
+    """Launch the batch of every dtype pair once; outputs stay on the device."""
     import torch
     from paper_1711_09791_gb300 import sepconv5 as sc5
     sc5.load()
-    shapes = synth.batch_shapes(3, 256)
-    sc5.autotune(1, [(dtype, dtype)])
-    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16,
-           "fp8e4m3": torch.float8_e4m3fn}[dtype]
-    es = sc5.DTYPE_BYTES[dtype]
-    imgs = []
+    shapes = synth.batch_shapes(3, N_IMAGES)
+    sc5.autotune(1, PAIRS)
+    stored = {}  # dtype -> list of device inputs
+    scales = []
     for i, (h, w) in enumerate(shapes):
-        x = torch.from_numpy(synth.image(3000 + i, h, w)).cuda()
-        s = 448.0 / float(x.abs().max()) if dtype == "fp8e4m3" else 1.0
-        pitch = -(-w * es // 16) * 16 // es
-        A = torch.zeros((3, h, pitch), dtype=tdt, device="cuda")
-        A[:, :, :w] = (x * s).to(tdt)
-        op = -(-(w - 4) // 4) * 4
-        out = torch.zeros((3, h - 4, op), dtype=tdt, device="cuda")
-        imgs.append({"in": A, "out": out, "H": h, "W": w, "in_pitch": pitch, "out_pitch": op,
-                     "k": synth.kernel_normalised(3000 + i), "in_scale": s, "out_scale": s})
-    plan = sc5.Plan(3, 64, 64, in_dtype=dtype)
-    b = sc5.Batch(plan, imgs)
-    b.launch()
-    torch.cuda.synchronize()
-    assert sc5.device_status() == 0
-    g = synth.rng(17)
-    idx = torch.arange(5, device="cuda")
-    for im in imgs:
-        h, w, m = im["H"], im["W"], 64
-        p, y, x = (torch.from_numpy(g.integers(0, n, m)).cuda() for n in (3, h - 4, w - 4))
-        # always include the four corners of plane 0
-        p[:4] = 0
-        y[:4] = torch.tensor([0, 0, h - 5, h - 5], device="cuda")
-        x[:4] = torch.tensor([0, w - 5, 0, w - 5], device="cuda")
-        s = im["in_scale"]
-        win = im["in"].float()[p[:, None, None], (y[:, None] + idx)[:, :, None], (x[:, None] + idx)[:, None, :]] / s
-        ref = oracle.direct(win.double().cpu().numpy(), np.asarray(im["k"], np.float64))[:, 0, 0]
-        got = (im["out"][p, y, x].float() / s).double().cpu().numpy()
-        if dtype == "f32":
-            assert U.max_abs(got, ref) <= U.FP32_TOL
-        else:
-            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, s, U.FP32_TOL))
-        assert not torch.isnan(im["out"][:, :, :w - 4].float()).any()
-    b.close()
-    plan.close()
+        x = synth.image(3000 + i, h, w)
+        s = synth.fp8_scale(x)
+        scales.append(s)
+        for dt in ("f32", "bf16", "f16", "fp8e4m3"):
+            codes = synth.to_storage(x, dt, s if dt == "fp8e4m3" else 1.0)
+            pitch = U.pitch_for(w, dt)
+            padded = np.zeros((3, h, pitch), codes.dtype)
+            padded[:, :, :w] = codes
+            stored.setdefault(dt, []).append(torch.from_numpy(_codes_view(padded)).cuda())
+    outs = {}
+    for dt, odt in PAIRS:
+        imgs = []
+        for i, (h, w) in enumerate(shapes):
+            s = scales[i] if dt == "fp8e4m3" else 1.0
+            op = U.pitch_for(w - 4, odt) if odt != "f32" else U.round_up(w - 4, 4)
+            out = U.empty_dev((3, h - 4, op + 4), odt)  # 4 sentinel columns past the row
+            imgs.append({"in": stored[dt][i], "out": out, "H": h, "W": w,
+                         "in_pitch": U.pitch_for(w, dt), "out_pitch": op + 4,
+                         "k": synth.kernel_normalised(3000 + i), "in_scale": s,
+                         "out_scale": s if odt == "fp8e4m3" else 1.0})
+        plan = sc5.Plan(3, 64, 64, in_dtype=dt, out_dtype=odt, ctas_per_sm=-1)
+        b = sc5.Batch(plan, imgs)  # times the CTA counts on itself, then captures the graph
+        b.launch()
+        torch.cuda.synchronize()
+        assert sc5.device_status() == 0
+        b.close()
+        plan.close()
+        outs[(dt, odt)] = imgs
+    del stored
+    return shapes, scales, outs
+
+
+def test_full_batch_every_pixel(batch_outputs):
+    shapes, scales, outs = batch_outputs
+    kernel = {p: ErrStats() for p in PAIRS}
+    e2e = {p: ErrStats() for p in PAIRS}
+    for i, (h, w) in enumerate(shapes):
+        x = synth.image(3000 + i, h, w)
+        k64 = synth.kernel_normalised(3000 + i).astype(np.float64)
+        ref_x = oracle.direct(x.astype(np.float64), k64)
+        refs = {"f32": ref_x}
+        for dt in ("bf16", "f16", "fp8e4m3"):
+            s = scales[i] if dt == "fp8e4m3" else 1.0
+            refs[dt] = oracle.direct(U.decode(synth.to_storage(x, dt, s), dt, s), k64)
+        for (dt, odt) in PAIRS:
+            im = outs[(dt, odt)][i]
+            raw = U.from_dev(im["out"], odt)
+            assert U.sentinel_intact(raw[:, :, w - 4:], odt), ("row padding written", dt, odt, h, w)
+            got = U.decode(raw[:, :, :w - 4], odt, im["out_scale"])
+            ref = refs[dt]
+            if odt == "f32":
+                assert U.max_abs(got, ref) <= U.FP32_TOL, (dt, odt, i, h, w)
+            else:
+                tol = U.stored_tolerance(ref, odt, im["out_scale"], U.FP32_TOL)
+                assert np.all(np.abs(got - ref) <= tol), (dt, odt, i, h, w)
+            kernel[(dt, odt)].add(got, ref)
+            e2e[(dt, odt)].add(got, ref_x)
+    report = {}
+    for (dt, odt) in PAIRS:
+        bound = ("max-abs 2e-4 (FP32 output)" if odt == "f32" else
+                 f"half an ulp of {odt} at the result + 2e-4 (in the stored code's units)")
+        report[f"{dt}->{odt}"] = {"vs_oracle_on_stored_input": kernel[(dt, odt)].report(),
+                                  "vs_oracle_on_fp32_input": e2e[(dt, odt)].report(), "bound": bound}
+    d = os.environ.get("SC5_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "error_batch.json"), "w") as f:
+            json.dump({"workload": f"{N_IMAGES} images, H and W log-uniform in [64,4096] (seed 3), "
+                                   "pixels uniform [0,255), per-image normalised k; every output pixel",
+                       "pairs": report}, f, indent=1)
+    print(json.dumps(report))
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])

@@ -152,11 +152,11 @@ def test_keep_border(sc5, algo):
     assert U.max_abs(out[:, 2:-2, 2:-2], ref[:, 2:-2, 2:-2]) <= U.FP32_TOL
 
 
-def test_c2_8192_full_size_sampled(sc5):
-    """3 x 8192 x 8192 FP32 in the launch configuration the benchmark times:
-    every output against fused == two-pass (bitwise, on the GPU), a band of
-    whole rows and columns at the edges against the oracle, and 30000 random
-    pixels against the oracle one by one."""
+def test_c2_8192_every_pixel(sc5):
+    """3 x 8192 x 8192 FP32 in the launch configuration the benchmark times
+    (the planner's default plan): every output pixel against the FP64 oracle,
+    in bands of 512 output rows (each oracle band reads its 4 halo rows from
+    the image), and fused == two-pass bit for bit."""
     import torch
     P, H, W = 3, 8192, 8192
     A = synth.image(2, H, W)
@@ -173,25 +173,16 @@ def test_c2_8192_full_size_sampled(sc5):
         outs[algo] = out
     assert sc5.device_status() == 0
     assert torch.equal(outs["fused"], outs["two_pass"])
-    fused = outs["fused"]
-    del outs
-    # edges: first/last 72 input rows and columns of each plane, in full
-    for rows in (slice(0, 72), slice(H - 72, H)):
-        ref = oracle.direct(A[:, rows, :].astype(np.float64), k64)
-        r0 = rows.start
-        got = fused[:, r0:r0 + 68, :].cpu().numpy()
-        assert U.max_abs(got, ref) <= U.FP32_TOL
-    for cols in (slice(0, 72), slice(W - 72, W)):
-        ref = oracle.direct(np.ascontiguousarray(A[:, :, cols]).astype(np.float64), k64)
-        c0 = cols.start
-        got = fused[:, :, c0:c0 + 68].cpu().numpy()
-        assert U.max_abs(got, ref) <= U.FP32_TOL
-    g = synth.rng(77)
-    pts = np.stack([g.integers(0, P, 30000), g.integers(0, H - 4, 30000), g.integers(0, W - 4, 30000)], 1)
-    want = oracle.points_f32(A, k, pts)
-    idx = torch.from_numpy(pts).cuda()
-    got = fused[idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
-    assert U.max_abs(got, want) <= U.FP32_TOL
+    fused = outs["fused"].cpu().numpy()
+    del outs, A_dev
+    worst = 0.0
+    for r0 in range(0, H - 4, 512):
+        r1 = min(H - 4, r0 + 512)
+        ref = oracle.direct(A[:, r0:r1 + 4, :].astype(np.float64), k64)
+        err = U.max_abs(fused[:, r0:r1, :], ref)
+        assert err <= U.FP32_TOL, (r0, err)
+        worst = max(worst, err)
+    assert np.isfinite(worst)
 
 
 # ------------------------------------------------------------------ reduced precision

@@ -70,14 +70,26 @@ def test_bench_helpers():
 
 
 def test_clock_sampler_parsing():
+    """Samples are time-stamped; the report covers the marked window plus the
+    first sample after it, and names the throttle reasons seen there."""
     import bench
     cs = bench.ClockSampler("0")
+    cs.PERIOD_MS = 0
     cs.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0})()
-    cs.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
-                "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
-                "garbage"]
+    cs.window = [10.0, 20.0]
+    cs.lines = [(5.0, "0, 900, 2070, 300.0, 0x0, Not Active, Active, Not Active, Not Active"),   # before
+                (11.0, "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active"),
+                (15.0, "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active"),
+                (16.0, "garbage"),
+                (21.0, "0, 2060, 2070, 800.0, 0x0, Not Active, Not Active, Not Active, Not Active"),  # next
+                (22.0, "0, 100, 2070, 80.0, 0x0, Active, Not Active, Not Active, Not Active")]        # later
     r = cs.stop()
-    assert r["sm_max_mhz"] == 2070 and r["samples"] == 2 and r["reasons"] == ["sw_power_cap"]
+    assert r["sm_max_mhz"] == 2070 and r["samples"] == 3 and r["samples_in_window"] == 3
+    assert r["sm_mhz"] == 2060 and r["reasons"] == ["sw_power_cap"]
+    empty = bench.ClockSampler("0")
+    empty.proc = cs.proc
+    empty.PERIOD_MS = 0
+    assert empty.stop()["reasons"] == ["no samples"]
 
 
 def test_binding_header_and_arguments():

@@ -8,6 +8,8 @@ oracle; requests that arrive while others run are merged into shared
 launches; the HBM budget bounds what is resident; unknown tickets, bad
 shapes and oversized requests are refused.
 """
+import json
+import os
 import threading
 
 import numpy as np
@@ -97,6 +99,77 @@ def test_same_alone_and_in_the_mix(sc5, dtype):
             assert U.max_abs(got, ref) <= U.FP32_TOL
         else:
             assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, 1.0, U.FP32_TOL))
+
+
+# The request sizes of the serving stream (640x480, 1920x1080, 4096x4096), two
+# of the largest among them: the heaviest merged launch the server makes.
+C5_MIX = [(4096, 4096), (480, 640), (1080, 1920), (480, 640), (4096, 4096), (1080, 1920), (480, 640),
+          (1080, 1920)]
+
+
+def test_c5_mix_with_4096_requests(sc5):
+    """BF16 requests of the serving stream's three sizes, two of them
+    4096 x 4096 (100.7 MB in and out each), submitted together under a 16 GB
+    budget with merged launches of up to 8 requests: every result equals its
+    solo sepconv5_run bit for bit and lies within the stored-format bound of
+    the FP64 oracle on its decoded input.  One 4096^2 image is also served as
+    FP32; with SC5_REPORT_DIR set, the measured errors of the BF16 and FP32
+    results against the oracle on the FP32 image are written to
+    error_serve.json."""
+    import torch
+    reqs = [_request(100 + i, H, W, "bf16") for i, (H, W) in enumerate(C5_MIX)]
+    srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype="bf16", max_inflight=64, n_streams=2, max_merge=8,
+                     batch_window_us=20000)
+    tickets = [srv.submit(r) for r, _ in reqs]
+    assert all(t is not None for t in tickets)
+    lats = [srv.poll(t, -1) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert all(lat is not None and lat > 0 for lat in lats)
+    assert stats["completed"] == len(reqs) and stats["merged_max"] > 1 and stats["launches"] < len(reqs)
+    assert stats["resident_peak_bytes"] <= 16 << 30
+    report = {}
+    for i, (req, padded) in enumerate(reqs):
+        H, W = req["H"], req["W"]
+        solo = _solo(sc5, req, "bf16")
+        assert torch.equal(solo[:, :, :W - 4], req["out"][:, :, :W - 4]), (H, W)
+        assert (req["out"][:, :, W - 4:] == -1).all(), "row padding written"
+        got = U.decode(U.from_dev(req["out"], "bf16")[:, :, :W - 4], "bf16")
+        ref = U.oracle_valid(padded, "bf16", req["k"], W=W)
+        assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, "bf16", 1.0, U.FP32_TOL)), (H, W)
+        if H == 4096 and not report:
+            x = synth.image(5000 + 100 + i, H, W)
+            ref_x = oracle_direct(x, req["k"])
+            report["bf16_served"] = _errors(got, ref_x, ref)
+            # the same image and taps served as FP32, one launch per request
+            f32_req, f32_padded = _request(100 + i, H, W, "f32")
+            srv32 = sc5.Server(hbm_budget_bytes=16 << 30, dtype="f32", merge=False)
+            t = srv32.submit(f32_req)
+            assert srv32.poll(t, -1) is not None
+            srv32.close()
+            got32 = U.from_dev(f32_req["out"], "f32")[:, :, :W - 4].astype(np.float64)
+            assert U.max_abs(got32, ref_x) <= U.FP32_TOL
+            report["f32_served"] = _errors(got32, ref_x, ref_x)
+    d = os.environ.get("SC5_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "error_serve.json"), "w") as f:
+            json.dump({"request": "3 x 4096 x 4096, pixels uniform [0,255), normalised k, served through "
+                                  "serve_submit / serve_poll", **report}, f, indent=1)
+
+
+def oracle_direct(x, k):
+    import oracle
+    return oracle.direct(x.astype(np.float64), np.asarray(k, np.float64))
+
+
+def _errors(got, ref_fp32_input, ref_stored_input):
+    def stats(ref):
+        d = np.abs(got - ref)
+        big = np.abs(ref) > 1.0
+        return {"max_abs": float(d.max()), "max_abs_over_255": float(d.max()) / 255.0,
+                "max_rel_where_abs_ref_gt_1": float((d[big] / np.abs(ref[big])).max())}
+    return {"vs_oracle_on_fp32_input": stats(ref_fp32_input), "vs_oracle_on_stored_input": stats(ref_stored_input)}
 
 
 def test_one_launch_per_request_mode(sc5):
