@@ -26,6 +26,7 @@ import hashlib
 import json
 import os
 import re
+import shutil
 import statistics
 import subprocess
 import sys
@@ -58,7 +59,8 @@ def parse():
     ap.add_argument("--case", default=None,
                     help="time one configuration instead of the contract run (the command the ncu captures use): "
                          "comma-separated key=value with keys dtype, out, algo (fused|two_pass|direct|reduce), "
-                         "layout (planar|hwc), planes, H, W, tile (THxTWxSTAGES), ctas; --steps timed launches "
+                         "layout (planar|hwc), planes, H, W, tile (THxTWxSTAGES), ctas, batch (N > 0: the first N "
+                         "images of the 256-image batch as one graph-replayed launch); --steps timed launches "
                          "after --warmup")
     return ap.parse_args()
 
@@ -143,10 +145,14 @@ class ClockSampler:
         self.window = [None, None]
 
     def start(self, wait_s: float = 5.0):
+        cmd = ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+               "-lms", str(self.PERIOD_MS)]
+        # nvidia-smi block-buffers a pipe: line buffering makes each sample arrive (and be
+        # time-stamped) when it is taken
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except OSError:
             self.proc = None
             return
@@ -450,66 +456,67 @@ def leg_batch(sc5, synth, stream, dtypes):
     return results
 
 
-def leg_serve(sc5, synth, n_req):
+def leg_serve(sc5, synth, n_req, link=None):
     """Serving stream: Poisson arrivals, sizes uniform over 640x480,
     1920x1080 and 4096x4096, per-request normalised k.  BF16 storage with
     continuous batching against FP32 with one launch per request, at 0.5x,
     0.8x and 0.95x of the measured saturation request rate of the BF16
     server.  Latency = completion of the result's copy to the host minus the
-    request's scheduled arrival."""
-    import queue as _q
-    import threading as _t
-
+    request's scheduled arrival.  Pinned buffers: 32 outputs per size class."""
     import torch
     sizes = synth.SERVE_SIZES
     out = {"workload": f"{n_req} requests per load, sizes {sizes} (H, W), Poisson arrivals",
            "budget_bytes": 16 << 30}
 
     def make_pool(dtype, n_buf):
+        """Per size class: one pinned input image and n_buf pinned output buffers."""
         tdt = {"bf16": torch.int16, "f32": torch.float32}[dtype]
-        es = sc5.DTYPE_BYTES[dtype]
         pool = []
         for ci, (h, w) in enumerate(sizes):
             x = synth.image(700 + ci, h, w)
             src = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16) if dtype == "bf16" else torch.from_numpy(x)
             src = src.contiguous().pin_memory()
-            q = _q.Queue()
-            for _ in range(n_buf):
-                q.put(torch.empty((P, h - 4, w - 4), dtype=tdt).pin_memory())
-            pool.append((src, q, h, w))
+            bufs = [torch.empty((P, h - 4, w - 4), dtype=tdt).pin_memory() for _ in range(n_buf)]
+            pool.append((src, bufs, h, w))
         return pool
 
     def run(dtype, merge, rate, n, pool, seed):
-        # merged launches of at most 8 requests: smaller groups keep both copy directions busy
-        # (saturation 3507 req/s against 3150 with no cap, same box)
+        """One thread submits every request at its scheduled arrival time.
+        Request j of size class c writes output buffer j mod n_buf of that
+        class; before reusing a buffer the thread polls the ticket that last
+        wrote it.  The requests (sc5_image structures) are built before the
+        clock starts, so the thread does no marshalling in the loop, and the
+        server's own clock gives each latency (submit to result on the host),
+        to which the submission's lateness against its arrival time is added."""
         srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype=dtype, max_inflight=64, n_streams=2, merge=merge,
                          max_merge=8 if merge else 0)
         stream_ = synth.serve_stream(seed, n, rate) if rate else [(0.0, c, s) for (_, c, s) in synth.serve_stream(seed, n, 1.0)]
-        lat = []
-        # one poller per size class: requests of one size finish in order, so a
-        # large request in flight does not hold back the buffers of small ones
-        tickets = [_q.Queue() for _ in pool]
-        px_done = [0]
-        lock = _t.Lock()
-
-        def poller(tq):
-            while True:
-                item = tq.get()
-                if item is None:
-                    return
-                t, t_arr, t_sub, buf, q, px = item
-                l_srv = srv.poll(t, -1)
-                with lock:
-                    lat.append((t_sub + l_srv * 1e-6) - t_arr)
-                    px_done[0] += px
-                q.put(buf)
-
-        ths = [_t.Thread(target=poller, args=(tq,)) for tq in tickets]
-        for th in ths:
-            th.start()
-        t_start = time.perf_counter()
+        n_buf = len(pool[0][1])
+        used = [0] * len(pool)
+        reqs = []
         for (t_arr, ci, kseed) in stream_:
-            src, q, h, w = pool[ci]
+            src, bufs, h, w = pool[ci]
+            reqs.append({"in": src, "out": bufs[used[ci] % n_buf], "H": h, "W": w, "in_pitch": w,
+                         "out_pitch": w - 4, "k": synth.kernel_normalised(kseed)})
+            used[ci] += 1
+        arr = sc5.make_images(reqs)
+        holder = [[None] * n_buf for _ in pool]  # (ticket, arrival, submit time) of the buffer's last user
+        lat = [[] for _ in pool]
+        late = []
+
+        def retire(item, ci):
+            tk, t_arr, t_sub = item
+            l_srv = srv.poll(tk, -1)
+            lat[ci].append(t_sub + l_srv * 1e-6 - t_arr)
+
+        count = [0] * len(pool)
+        t_start = time.perf_counter()
+        for j, (t_arr, ci, _) in enumerate(stream_):
+            slot = count[ci] % n_buf
+            count[ci] += 1
+            if holder[ci][slot] is not None:
+                retire(holder[ci][slot], ci)
+                holder[ci][slot] = None
             target = t_start + t_arr
             while True:
                 now = time.perf_counter()
@@ -517,40 +524,59 @@ def leg_serve(sc5, synth, n_req):
                     break
                 if target - now > 2e-4:
                     time.sleep(target - now - 1e-4)
-            buf = q.get()
-            req = {"in": src, "out": buf, "H": h, "W": w, "in_pitch": w, "out_pitch": w - 4,
-                   "k": synth.kernel_normalised(kseed)}
             t_sub = time.perf_counter()
-            tk = srv.submit(req)
+            tk = srv.submit_image(arr[j])
             while tk is None:
                 time.sleep(1e-4)
-                tk = srv.submit(req)
-            tickets[ci].put((tk, target, t_sub, buf, q, h * w))
-        for tq in tickets:
-            tq.put(None)
-        for th in ths:
-            th.join()
+                tk = srv.submit_image(arr[j])
+            late.append(t_sub - target)
+            holder[ci][slot] = (tk, target, t_sub)
+        for ci in range(len(pool)):
+            for item in holder[ci]:
+                if item is not None:
+                    retire(item, ci)
         wall = time.perf_counter() - t_start
         st = srv.stats()
         srv.close()
-        lat_ms = np.array(lat) * 1e3
-        return {"offered_req_s": round(rate, 1) if rate else None, "achieved_req_s": round(n / wall, 1),
-                "mpix_s": round(px_done[0] / wall / 1e6, 1), "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat_ms, 99)), 3), "launches": st["launches"],
-                "merged_max": st["merged_max"], "resident_peak_bytes": st["resident_peak_bytes"],
-                "phases_ms": {f"{ph}_p{q}": round(st[f"{ph}_us_p{q}"] / 1e3, 3)
-                              for ph in ("queue", "stage", "run") for q in (50, 99)}}
+        px = sum(pool[ci][2] * pool[ci][3] for (_, ci, _) in stream_)
+        all_ms = np.concatenate([np.array(v) for v in lat]) * 1e3
+        res = {"offered_req_s": round(rate, 1) if rate else None, "achieved_req_s": round(n / wall, 1),
+               "mpix_s": round(px / wall / 1e6, 1), "p50_ms": round(float(np.percentile(all_ms, 50)), 3),
+               "p99_ms": round(float(np.percentile(all_ms, 99)), 3), "launches": st["launches"],
+               "merged_max": st["merged_max"], "resident_peak_bytes": st["resident_peak_bytes"],
+               "submit_late_p99_ms": round(float(np.percentile(np.array(late) * 1e3, 99)), 3),
+               "per_size": {f"{h}x{w}": {"p50_ms": round(float(np.percentile(np.array(v) * 1e3, 50)), 3),
+                                         "p99_ms": round(float(np.percentile(np.array(v) * 1e3, 99)), 3)}
+                            for (_, _, h, w), v in zip(pool, lat) if v},
+               "phases_ms": {f"{ph}_p{q}": round(st[f"{ph}_us_p{q}"] / 1e3, 3)
+                             for ph in ("queue", "stage", "run") for q in (50, 99)}}
+        return res
 
-    pool_bf = make_pool("bf16", 24)
+    # the submitting thread waits for arrival times with the interpreter lock
+    # held for at most ~100 us at a time; a short switch interval lets the
+    # pollers take it back promptly
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)
+    pool_bf = make_pool("bf16", 32)
     sat = run("bf16", True, 0.0, min(n_req, 2000), pool_bf, 11)
     rate_sat = sat["achieved_req_s"]
+    # the link ceiling of this mix: each request's input crosses host->device
+    # and its output device->host, both directions at once
+    es = sc5.DTYPE_BYTES["bf16"]
+    bytes_per_req = sum(P * h * w * es + P * (h - 4) * (w - 4) * es for h, w in sizes) / len(sizes)
+    sat["link_bytes_per_req"] = int(bytes_per_req)
+    if link and link.get("both_gbs"):
+        both = max(link["both_gbs"], link.get("both_2streams_gbs", 0.0))
+        sat["link_ceiling_req_s"] = round(both * 1e9 / bytes_per_req, 1)
+        sat["frac_of_link"] = round(rate_sat * bytes_per_req / (both * 1e9), 4)
     out["saturation_bf16_merged"] = sat
-    pool_f32 = make_pool("f32", 24)
+    pool_f32 = make_pool("f32", 32)
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
         out[f"load_{frac}"] = {"bf16_merged": run("bf16", True, rate, n_req, pool_bf, 20 + int(frac * 100)),
                                "f32_per_request": run("f32", False, rate, n_req, pool_f32, 20 + int(frac * 100))}
     del pool_bf, pool_f32
+    sys.setswitchinterval(old_switch)
     return out
 
 
@@ -560,12 +586,12 @@ def leg_serve(sc5, synth, n_req):
 def parse_case(spec: str) -> dict:
     """`--case` key=value list -> options (defaults: 3 x 8192 x 8192 FP32 fused, planar)."""
     c = {"dtype": "f32", "out": None, "algo": "fused", "layout": "planar", "planes": P, "H": H, "W": W,
-         "tile": "", "ctas": 0}
+         "tile": "", "ctas": 0, "batch": 0}
     for item in filter(None, (x.strip() for x in spec.split(","))):
         key, _, val = item.partition("=")
         if key not in c:
             raise SystemExit(f"--case: unknown key {key!r} (keys: {', '.join(c)})")
-        c[key] = int(val) if key in ("planes", "H", "W", "ctas") else val
+        c[key] = int(val) if key in ("planes", "H", "W", "ctas", "batch") else val
     c["out"] = c["out"] or c["dtype"]
     return c
 
@@ -581,6 +607,8 @@ def run_case(args):
     from paper_1711_09791_gb300 import synth
     c = parse_case(args.case)
     sc5.load()
+    if c["batch"] > 0:
+        return run_case_batch(args, c, sc5, synth)
     Pc, Hc, Wc, dt, odt = c["planes"], c["H"], c["W"], c["dtype"], c["out"]
     es, eo = sc5.DTYPE_BYTES[dt], sc5.DTYPE_BYTES[odt]
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}
@@ -626,6 +654,52 @@ def run_case(args):
     alg = Pc * Hc * Wc * es + Pc * Ho * Wo * eo
     return {"case": c, "ms": round(ms, 5), "gbs": round(alg / ms / 1e6, 1), "mpix_s": round(Hc * Wc / ms / 1e3, 1),
             "algorithmic_bytes": alg, "plan": info, "launches": len(times)}
+
+
+def run_case_batch(args, c, sc5, synth):
+    """The first N images of the 256-image batch (as the batch leg builds
+    them), one persistent launch replayed from a CUDA graph: tile shape from
+    the override or the built-in default, CTAs per SM as given (0: the
+    shape's default); median CUDA-event time of --steps replays."""
+    import torch
+    dt, odt = c["dtype"], c["out"]
+    shapes = synth.batch_shapes(3, 256)[:c["batch"]]
+    x_dev = [torch.from_numpy(synth.image(3000 + i, h, w)).cuda() for i, (h, w) in enumerate(shapes)]
+    scales = [448.0 / float(x.abs().max()) for x in x_dev]
+    imgs, keep = _batch_images(sc5, synth, dt, shapes, x_dev, scales)
+    del x_dev
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16, "fp8e4m3": torch.float8_e4m3fn}
+    for im in imgs:
+        im["out"] = torch.empty((P, im["H"] - 4, im["out_pitch"]), dtype=tdt[odt], device="cuda")
+        if odt == "f32":
+            im["out_scale"] = 1.0
+    th = tw = st = 0
+    if c["tile"]:
+        th, tw, st = (int(v) for v in c["tile"].split("x"))
+    plan = sc5.Plan(P, 64, 64, in_dtype=dt, out_dtype=odt, tile_h=th, tile_w=tw, stages=st, ctas_per_sm=c["ctas"])
+    b = sc5.Batch(plan, imgs)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 0)):
+        b.launch(stream)
+    times = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(args.steps, 1)):
+        e0.record(stream)
+        b.launch(stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if sc5.device_status(stream) != 0:
+        raise SystemExit("a kernel reported a device error")
+    info = b.info()
+    b.close()
+    plan.close()
+    ms = statistics.median(times)
+    es, eo = sc5.DTYPE_BYTES[dt], sc5.DTYPE_BYTES[odt]
+    alg = sum(P * h * w * es + P * (h - 4) * (w - 4) * eo for h, w in shapes)
+    px = sum(h * w for h, w in shapes)
+    return {"case": c, "ms": round(ms, 5), "gbs": round(alg / ms / 1e6, 1), "mpix_s": round(px / ms / 1e3, 1),
+            "algorithmic_bytes": alg, "batch": info, "launches": len(times)}
 
 
 # ------------------------------------------------------------------ main legs
@@ -819,7 +893,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if "paper" in legs:
             extras["paper_sizes"] = leg_paper_sizes(sepconv5, stream)
         if "c5" in legs:
-            extras["serve_c5"] = leg_serve(sepconv5, synth, args.serve_requests)
+            extras["serve_c5"] = leg_serve(sepconv5, synth, args.serve_requests, e2e.get("link"))
     if rank != 0:
         return None
     line = {

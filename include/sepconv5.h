@@ -394,15 +394,11 @@ typedef struct {
     int32_t dtype;            /* storage format of inputs and outputs */
     int32_t planes;           /* planes per image */
     int32_t n_streams;        /* compute streams used round robin (>= 1) */
-    int32_t max_merge;        /* most requests merged into one launch (0 = no limit).  Small
-                                 groups keep both copy directions busy: with requests of
-                                 640x480, 1920x1080 and 4096x4096, 8 gave the highest
-                                 saturation (3507 req/s against 3150 with no limit) and the
-                                 shorter tail */
+    int32_t max_merge;        /* most requests merged into one launch (0 = no limit) */
     int32_t merge;            /* 1 = continuous batching, 0 = one launch per request */
     int32_t batch_window_us;  /* hold admitted requests up to this long (or until max_merge
                                  are waiting) before launching them together; 0 = launch
-                                 whatever is admitted as soon as a stream slot is free */
+                                 whatever one pass of the scheduler admitted at once */
 } sc5_serve_cfg;
 
 typedef struct {
@@ -412,11 +408,10 @@ typedef struct {
     /* Where completed requests spent their time (microseconds, host clock,
      * median and 99th percentile over the last 2^20 completions; 0 before the
      * first):  queue = submitted until admitted (waiting for arena space or an
-     * in-flight slot; the input copy is enqueued at admission);  stage =
-     * admitted until its launch is enqueued (waiting for a compute-stream slot
-     * or the merge window);  run = launch enqueued until the completion thread
-     * sees the output copy done (input copy still in flight, kernel, output
-     * copy, polling). */
+     * in-flight slot);  stage = admitted until its launch is enqueued (the
+     * input copy is enqueued at admission; a batching window adds its wait);
+     * run = launch enqueued until the completion thread sees the request's
+     * output copy done (input copy still in flight, kernel, output copy). */
     double queue_us_p50, queue_us_p99, stage_us_p50, stage_us_p99, run_us_p50, run_us_p99;
 } sc5_serve_stats;
 
@@ -429,15 +424,19 @@ typedef struct {
 SC5_API sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out);
 
 /* Queue one request.  req->in and req->out are HOST pointers to
- * [planes][H][pitch] images of the server's dtype; the server reads `in`
+ * [planes][H][pitch] images of the server's dtype, in page-locked memory
+ * (cudaMallocHost, cudaHostAlloc or cudaHostRegister); the server reads `in`
  * and writes the W-4 output values of each row of `out` (its row padding is
  * left as it was) asynchronously, so both must stay valid until serve_poll
- * returns SC5_OK for the ticket (pinned memory gives the fastest copies).
+ * returns SC5_OK for the ticket.  The output buffer is named here rather
+ * than at serve_poll: its copy is issued behind the kernel as soon as the
+ * request is launched, and lands while the caller is not yet polling.
  * A request that fits the budget but not the arena's free space waits in the
  * queue until earlier requests retire.  Returns SC5_EAGAIN when 65536
  * requests are already queued (back-pressure: retry later), SC5_EINVAL for a
- * bad shape, non-finite taps, a scale that is not finite and > 0, or a
- * request that needs more than the whole budget. */
+ * bad shape, non-finite taps, a scale that is not finite and > 0, a host
+ * buffer that is not page-locked, or a request that needs more than the
+ * whole budget. */
 SC5_API sc5_status serve_submit(sc5_server srv, const sc5_image *req, uint64_t *ticket);
 
 /* Wait up to timeout_us (0 = just test, <0 = forever) for a ticket.  SC5_OK:

@@ -1,23 +1,29 @@
 // sc5_serve.cpp -- serving runtime: continuous batching of convolution
 // requests on one GPU.
 //
-// Requests (host images of any size, each with its own 5 taps) are queued by
-// serve_submit.  A scheduler thread admits them in arrival order while the
-// resident arena (a fixed device allocation of hbm_budget_bytes made at
-// start) has room for their input and output and fewer than max_inflight
-// are admitted; each admitted request's input is copied to the device on a
-// copy stream.  What has been admitted and not yet launched is merged, up to
-// max_merge requests at a time, into one persistent launch of the fused batch
-// kernel (per-image descriptors + tile work-list), issued on the next of
-// n_streams compute streams after the requests' copies have landed; the
-// output values (not the rows' padding) are copied back to the requests' host
-// buffers on a second copy stream.  At most two launches
-// per compute stream are in flight: while they run, newly arriving requests
-// are admitted and staged, and go out together in the next launch.  A
-// completion thread retires launches as their last copy lands, frees their
-// arena blocks (which lets waiting requests in) and time-stamps every
-// request.  Each tile's arithmetic does not depend on what else is in the
-// launch, so a request's result is the same alone and in any mix.
+// Requests (page-locked host images of any size, each with its own 5 taps)
+// are queued by serve_submit.  A scheduler thread admits them in arrival
+// order while the resident arena (one device allocation of hbm_budget_bytes
+// made at start) has room for their input and output and fewer than
+// max_inflight are admitted, and issues each admitted request's input copy
+// on the copy stream at once.  Everything admitted in one pass of the
+// scheduler (or, with a batching window, within the window) goes out as one
+// persistent launch of the fused batch kernel (per-image descriptors + tile
+// work-list, up to max_merge requests), issued on the next of n_streams
+// compute streams behind device-side waits on those requests' input copies:
+// the kernel starts the moment the last input lands, with no host round
+// trip.  Behind the kernel, each request's output values (not the rows'
+// padding) are copied back to its host buffer on a second copy stream,
+// smallest request first, and an event is recorded after each copy.
+//
+// No lock is held while a CUDA call is issued.  A completion thread waits on
+// those events in the order the copies were issued (blocking-sync events:
+// the thread sleeps until the copy lands, there is no polling loop), and
+// completes each request on its own: time stamp, arena blocks freed (which
+// lets waiting requests in), ticket marked done.  A launch's descriptor
+// block is freed with its last request.  Each tile's arithmetic does not
+// depend on what else is in the launch, so a request's result is the same
+// alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -25,7 +31,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
-#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -41,9 +46,14 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr int kSlots = 8;                       // descriptor slots (launches in flight)
-constexpr size_t kSlotBytes = 8u << 20;         // descriptors + tile list per launch
-constexpr int kMaxQueued = 1 << 16;             // pending requests before back-pressure
+constexpr size_t kDescBytes = 64u << 20;       // descriptor + work-list area (device, pinned host mirror)
+constexpr size_t kLaunchDescCap = 8u << 20;    // descriptor bytes one merged launch may take
+constexpr int kMaxQueued = 1 << 16;            // pending requests before back-pressure
+
+struct Launch {
+    size_t desc_off = 0, desc_bytes = 0;  // block of the descriptor area (bytes 0: none)
+    int remaining = 0;                    // requests of the launch not yet completed
+};
 
 struct Request {
     uint64_t id = 0;
@@ -51,17 +61,22 @@ struct Request {
     size_t in_bytes = 0, out_bytes = 0;
     size_t in_off = 0, out_off = 0;
     Clock::time_point t_submit, t_admit, t_launch, t_done;
-    cudaEvent_t h2d = nullptr;
+    cudaEvent_t h2d = nullptr;   // the input copy has landed
+    cudaEvent_t done_ev = nullptr;  // the output copy has landed (blocking sync)
+    std::shared_ptr<Launch> launch;
     bool done = false;
     sc5_status status = SC5_OK;
 };
 
-struct Launch {
-    std::vector<std::shared_ptr<Request>> reqs;
-    int slot = -1;
-    int stream = 0;
-    cudaEvent_t done = nullptr;
-};
+bool is_page_locked(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error the query may leave
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
 
 }  // namespace
 
@@ -76,42 +91,51 @@ struct sc5_server_s {
     Arena arena;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     std::vector<cudaStream_t> s_comp;
-    std::vector<int> inflight_per_stream;
-    unsigned char *slot_dev = nullptr;
-    unsigned char *slot_host = nullptr;
-    std::vector<bool> slot_busy;
-    std::vector<cudaEvent_t> event_pool;
+    unsigned char *desc_dev = nullptr;
+    unsigned char *desc_host = nullptr;
+    Arena desc_arena;
+
+    std::mutex ev_mu;  // event pools (scheduler and completion threads)
+    std::vector<cudaEvent_t> plain_events, blocking_events;
 
     std::mutex mu;
-    std::condition_variable cv_sched, cv_done;
-    std::deque<std::shared_ptr<Request>> pending;   // submitted, not admitted
-    std::vector<std::shared_ptr<Request>> staged;   // admitted, input copy issued, not launched
-    Clock::time_point staged_since;                  // admission time of the oldest staged request
-    std::deque<Launch> running;                      // launched, not retired
+    std::condition_variable cv_sched, cv_done, cv_compl;
+    std::deque<std::shared_ptr<Request>> pending;      // submitted, not admitted
+    std::deque<std::shared_ptr<Request>> issued;       // output copy issued, not completed (issue order)
     std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
     uint64_t next_id = 1;
     int admitted = 0;
-    bool stop = false;
+    bool stop = false, sched_done = false;
     sc5_serve_stats stats{};
     std::thread sched, compl_;
-    int next_stream = 0;
     int fault_sched_delay_ms = 0;  // host-side fault injection (SC5_SERVE_FAULT)
     PhaseLog phases;
 
-    cudaEvent_t get_event()
+    // scheduler-thread state (no lock)
+    std::vector<std::shared_ptr<Request>> staged;  // input copy issued, not launched
+    Clock::time_point staged_since;
+    int next_stream = 0;
+
+    cudaEvent_t get_event(bool blocking)
     {
-        if (!event_pool.empty()) {
-            cudaEvent_t e = event_pool.back();
-            event_pool.pop_back();
-            return e;
+        {
+            std::lock_guard<std::mutex> lk(ev_mu);
+            auto &pool = blocking ? blocking_events : plain_events;
+            if (!pool.empty()) {
+                cudaEvent_t e = pool.back();
+                pool.pop_back();
+                return e;
+            }
         }
         cudaEvent_t e = nullptr;
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming | (blocking ? cudaEventBlockingSync : 0));
         return e;
     }
-    void put_event(cudaEvent_t e)
+    void put_event(cudaEvent_t e, bool blocking)
     {
-        if (e) event_pool.push_back(e);
+        if (!e) return;
+        std::lock_guard<std::mutex> lk(ev_mu);
+        (blocking ? blocking_events : plain_events).push_back(e);
     }
 
     size_t need_bytes(const sc5_image &im) const
@@ -123,88 +147,107 @@ struct sc5_server_s {
 
     void scheduler_loop();
     void completion_loop();
-    // Merge staged requests into one launch (called with mu held).
-    void launch_staged(std::unique_lock<std::mutex> &lk);
+    void launch_group(std::vector<std::shared_ptr<Request>> group);
 };
 
 void sc5_server_s::scheduler_loop()
 {
     cudaSetDevice(device);
     const int es = dtype_bytes(cfg.dtype);
-    std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-        // 1. admission, in arrival order
-        if (fault_sched_delay_ms > 0 && !pending.empty()) {
-            lk.unlock();
-            std::this_thread::sleep_for(std::chrono::milliseconds(fault_sched_delay_ms));
-            lk.lock();
-        }
-        while (!pending.empty() && admitted < cfg.max_inflight) {
-            auto r = pending.front();
-            size_t in_off = 0, out_off = 0;
-            if (!arena.alloc(r->in_bytes, &in_off)) break;
-            if (!arena.alloc(r->out_bytes, &out_off)) {
-                arena.release(in_off, r->in_bytes);
-                break;
+        // 1. admission, in arrival order (under the lock: no CUDA calls)
+        std::vector<std::shared_ptr<Request>> admit;
+        bool stopping = false;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (fault_sched_delay_ms > 0 && !pending.empty()) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::milliseconds(fault_sched_delay_ms));
+                lk.lock();
             }
-            pending.pop_front();
-            r->in_off = in_off;
-            r->out_off = out_off;
-            r->t_admit = Clock::now();
-            ++admitted;
-            stats.resident_peak_bytes = std::max(stats.resident_peak_bytes, arena.used());
-            r->h2d = get_event();
-            cudaMemcpyAsync(arena_base + in_off, r->img.in,
+            while (!pending.empty() && admitted < cfg.max_inflight) {
+                auto r = pending.front();
+                size_t in_off = 0, out_off = 0;
+                if (!arena.alloc(r->in_bytes, &in_off)) break;
+                if (!arena.alloc(r->out_bytes, &out_off)) {
+                    arena.release(in_off, r->in_bytes);
+                    break;
+                }
+                pending.pop_front();
+                r->in_off = in_off;
+                r->out_off = out_off;
+                r->t_admit = Clock::now();
+                ++admitted;
+                stats.resident_peak_bytes = std::max(stats.resident_peak_bytes, arena.used());
+                admit.push_back(r);
+            }
+            stopping = stop;
+            if (admit.empty() && staged.empty()) {
+                if (stopping && pending.empty()) break;
+                // nothing to do until a submit, a completion (arena space) or stop
+                cv_sched.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+        }
+        // 2. input copies, issued at once on the copy stream
+        for (auto &r : admit) {
+            r->h2d = get_event(false);
+            cudaMemcpyAsync(arena_base + r->in_off, r->img.in,
                             static_cast<size_t>(cfg.planes) * r->img.H * r->img.in_pitch * es,
                             cudaMemcpyHostToDevice, s_h2d);
             cudaEventRecord(r->h2d, s_h2d);
             if (staged.empty()) staged_since = Clock::now();
             staged.push_back(r);
-            if (!cfg.merge) break;  // one request per launch: launch it right away
         }
-        // 2. merge what is staged into one launch when a stream slot is free
-        if (!staged.empty()) {
-            const int s = next_stream;
-            const bool slot_free = std::find(slot_busy.begin(), slot_busy.end(), false) != slot_busy.end();
+        // 3. merge what is staged into launches (all of it at once, up to
+        // max_merge per launch), unless a batching window holds it a little
+        // longer
+        while (!staged.empty()) {
             const bool window_over =
-                !cfg.merge || cfg.batch_window_us <= 0 || stop ||
+                !cfg.merge || cfg.batch_window_us <= 0 || stopping ||
                 (cfg.max_merge > 0 && static_cast<int>(staged.size()) >= cfg.max_merge) ||
                 Clock::now() - staged_since >= std::chrono::microseconds(cfg.batch_window_us);
-            if (slot_free && inflight_per_stream[s] < 2 && window_over) {
-                launch_staged(lk);
-                if (!staged.empty()) staged_since = Clock::now();
-                continue;
+            if (!window_over) break;
+            const size_t cap = !cfg.merge ? 1 : cfg.max_merge > 0 ? static_cast<size_t>(cfg.max_merge) : staged.size();
+            std::vector<std::shared_ptr<Request>> group;
+            size_t bytes = 0, taken = 0;
+            for (; taken < staged.size() && group.size() < cap; ++taken) {
+                const auto &r = staged[taken];
+                // upper bound on this image's share: descriptor + smallest-tile work-list
+                const size_t tiles =
+                    static_cast<size_t>(cfg.planes) * ((r->img.H - 4 + 31) / 32) * ((r->img.W - 4 + 127) / 128);
+                const size_t add = sizeof(ImgDesc) + tiles * sizeof(TileRec);
+                if (!group.empty() && bytes + add + kArenaAlign > kLaunchDescCap) break;
+                bytes += add;
+                group.push_back(r);
             }
+            staged.erase(staged.begin(), staged.begin() + static_cast<std::ptrdiff_t>(taken));
+            if (!staged.empty()) staged_since = Clock::now();
+            launch_group(std::move(group));
         }
-        if (stop && pending.empty() && staged.empty()) break;
-        cv_sched.wait_for(lk, std::chrono::microseconds(200));
+        if (!staged.empty()) {
+            // a batching window is open: come back when it closes (or earlier on a submit)
+            std::unique_lock<std::mutex> lk(mu);
+            const auto left = std::chrono::microseconds(cfg.batch_window_us) - (Clock::now() - staged_since);
+            if (left > Clock::duration::zero() && !stop) cv_sched.wait_for(lk, left);
+        }
     }
+    std::lock_guard<std::mutex> lk(mu);
+    sched_done = true;
+    cv_compl.notify_all();
 }
 
-void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
+void sc5_server_s::launch_group(std::vector<std::shared_ptr<Request>> group)
 {
     const int es = dtype_bytes(cfg.dtype);
-    int slot = static_cast<int>(std::find(slot_busy.begin(), slot_busy.end(), false) - slot_busy.begin());
-    // take requests while their work-list fits the descriptor slot
-    std::vector<std::shared_ptr<Request>> group;
     std::vector<sc5_image> imgs;
-    size_t bytes = 0;
-    const size_t cap = !cfg.merge ? 1 : cfg.max_merge > 0 ? static_cast<size_t>(cfg.max_merge) : staged.size();
-    size_t taken = 0;
-    for (; taken < staged.size() && group.size() < cap; ++taken) {
-        auto &r = staged[taken];
-        // upper bound on this image's share: descriptor + smallest-tile work-list
-        const size_t tiles = static_cast<size_t>(cfg.planes) * ((r->img.H - 4 + 31) / 32) * ((r->img.W - 4 + 127) / 128);
-        const size_t add = sizeof(ImgDesc) + tiles * sizeof(TileRec);
-        if (!group.empty() && bytes + add + kArenaAlign > kSlotBytes) break;
-        bytes += add;
+    imgs.reserve(group.size());
+    for (auto &r : group) {
         sc5_image d = r->img;
         d.in = arena_base + r->in_off;
         d.out = arena_base + r->out_off;
         imgs.push_back(d);
-        group.push_back(r);
     }
-    staged.erase(staged.begin(), staged.begin() + taken);
     sc5_plan_desc pd{};
     pd.planes = cfg.planes;
     pd.in_dtype = pd.out_dtype = cfg.dtype;
@@ -220,21 +263,38 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
         fused_shape(cfg.dtype, cfg.dtype, idx, &sh);
         st = build_batch(pd, static_cast<int>(imgs.size()), imgs.data(), sh, &blob, &ntiles, &toff);
     }
-    if (st == SC5_OK && blob.size() > kSlotBytes) st = SC5_ENOMEM;
+    if (st == SC5_OK && blob.size() > kLaunchDescCap) st = SC5_ENOMEM;
+    auto L = std::make_shared<Launch>();
+    L->remaining = static_cast<int>(group.size());
+    if (st == SC5_OK) {
+        // a block of the descriptor area: wait for earlier launches to retire if it is full
+        std::unique_lock<std::mutex> lk(mu);
+        while (!desc_arena.alloc(blob.size(), &L->desc_off)) {
+            if (issued.empty()) {  // nothing in flight will free space: cannot happen below the cap
+                st = SC5_ENOMEM;
+                break;
+            }
+            cv_sched.wait_for(lk, std::chrono::milliseconds(1));
+        }
+        if (st == SC5_OK) L->desc_bytes = blob.size();
+    }
     const int s = next_stream;
     next_stream = (next_stream + 1) % static_cast<int>(s_comp.size());
-    Launch L;
-    L.reqs = group;
-    L.stream = s;
-    L.slot = slot;
-    L.done = get_event();
     cudaStream_t cs = s_comp[s];
     const auto t_launch = Clock::now();
-    for (auto &r : group) r->t_launch = t_launch;
+    for (auto &r : group) {
+        r->t_launch = t_launch;
+        r->launch = L;
+    }
+    // outputs go back smallest first, so that small requests do not wait
+    // behind a large one of the same launch
+    std::stable_sort(group.begin(), group.end(),
+                     [](const std::shared_ptr<Request> &a, const std::shared_ptr<Request> &b) {
+                         return a->out_bytes < b->out_bytes;
+                     });
     if (st == SC5_OK) {
-        slot_busy[slot] = true;
-        unsigned char *hs = slot_host + static_cast<size_t>(slot) * kSlotBytes;
-        unsigned char *ds = slot_dev + static_cast<size_t>(slot) * kSlotBytes;
+        unsigned char *hs = desc_host + L->desc_off;
+        unsigned char *ds = desc_dev + L->desc_off;
         std::memcpy(hs, blob.data(), blob.size());
         cudaMemcpyAsync(ds, hs, blob.size(), cudaMemcpyHostToDevice, cs);
         for (auto &r : group) cudaStreamWaitEvent(cs, r->h2d, 0);
@@ -243,7 +303,9 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
         cudaError_t e = launch_fused_batch(cfg.dtype, cfg.dtype, idx, reinterpret_cast<const ImgDesc *>(ds),
                                            reinterpret_cast<const TileRec *>(ds + toff), ntiles, grid, cs);
         if (e != cudaSuccess) st = SC5_ECUDA;
-        cudaEvent_t kdone = get_event();
+    }
+    if (st == SC5_OK) {
+        cudaEvent_t kdone = get_event(false);
         cudaEventRecord(kdone, cs);
         cudaStreamWaitEvent(s_d2h, kdone, 0);
         // results go back as their W-4 valid values per row: the caller's row
@@ -253,62 +315,66 @@ void sc5_server_s::launch_staged(std::unique_lock<std::mutex> &)
             cudaMemcpy2DAsync(r->img.out, pitch_b, arena_base + r->out_off, pitch_b,
                               static_cast<size_t>(r->img.W - 4) * es,
                               static_cast<size_t>(cfg.planes) * (r->img.H - 4), cudaMemcpyDeviceToHost, s_d2h);
+            r->done_ev = get_event(true);
+            cudaEventRecord(r->done_ev, s_d2h);
         }
-        cudaEventRecord(L.done, s_d2h);
-        put_event(kdone);  // its record/wait are already enqueued
+        put_event(kdone, false);  // its record and the wait on it are already enqueued
     } else {
-        L.slot = -1;
-        cudaEventRecord(L.done, cs);
-        for (auto &r : group) r->status = st;
+        // nothing was launched: the requests complete with the error once
+        // their input copies (which still write the arena) have landed
+        for (auto &r : group) cudaStreamWaitEvent(cs, r->h2d, 0);
+        for (auto &r : group) {
+            r->status = st;
+            r->done_ev = get_event(true);
+            cudaEventRecord(r->done_ev, cs);
+        }
     }
-    ++inflight_per_stream[s];
-    ++stats.launches;
-    stats.merged_max = std::max<uint64_t>(stats.merged_max, group.size());
-    running.push_back(std::move(L));
-    cv_done.notify_all();
+    for (auto &r : group) {  // the waits on the input copies are enqueued
+        put_event(r->h2d, false);
+        r->h2d = nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &r : group) issued.push_back(r);
+        ++stats.launches;
+        stats.merged_max = std::max<uint64_t>(stats.merged_max, group.size());
+    }
+    cv_compl.notify_one();
 }
 
 void sc5_server_s::completion_loop()
 {
     cudaSetDevice(device);
-    std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-        bool progressed = false;
-        for (auto it = running.begin(); it != running.end();) {
-            const cudaError_t q = cudaEventQuery(it->done);
-            if (q == cudaErrorNotReady) {
-                ++it;
-                continue;
-            }
-            const auto now = Clock::now();
-            for (auto &r : it->reqs) {
-                if (q != cudaSuccess && r->status == SC5_OK) r->status = SC5_ECUDA;
-                r->t_done = now;
-                r->done = true;
-                phases.add(r->t_admit - r->t_submit, r->t_launch - r->t_admit, now - r->t_launch);
-                arena.release(r->in_off, r->in_bytes);
-                arena.release(r->out_off, r->out_bytes);
-                put_event(r->h2d);
-                r->h2d = nullptr;
-                --admitted;
-                ++stats.completed;
-            }
-            if (it->slot >= 0) slot_busy[it->slot] = false;
-            --inflight_per_stream[it->stream];
-            put_event(it->done);
-            it = running.erase(it);
-            progressed = true;
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_compl.wait(lk, [&] { return !issued.empty() || sched_done; });
+            if (issued.empty()) break;  // the scheduler has finished and everything completed
+            r = issued.front();
         }
-        if (progressed) {
-            cv_done.notify_all();
-            cv_sched.notify_all();
+        // sleeps until the copy lands (blocking-sync event); outside the lock
+        const cudaError_t q = cudaEventSynchronize(r->done_ev);
+        const auto now = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            issued.pop_front();
+            if (q != cudaSuccess && r->status == SC5_OK) r->status = SC5_ECUDA;
+            r->t_done = now;
+            r->done = true;
+            phases.add(r->t_admit - r->t_submit, r->t_launch - r->t_admit, now - r->t_launch);
+            arena.release(r->in_off, r->in_bytes);
+            arena.release(r->out_off, r->out_bytes);
+            --admitted;
+            ++stats.completed;
+            if (--r->launch->remaining == 0 && r->launch->desc_bytes)
+                desc_arena.release(r->launch->desc_off, r->launch->desc_bytes);
+            r->launch.reset();
         }
-        if (stop && running.empty() && pending.empty() && staged.empty()) break;
-        if (!progressed) {
-            lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
-            lk.lock();
-        }
+        put_event(r->done_ev, true);
+        r->done_ev = nullptr;
+        cv_done.notify_all();
+        cv_sched.notify_all();
     }
 }
 
@@ -335,8 +401,8 @@ extern "C" sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out)
     cudaError_t e = cudaMalloc(&s->arena_base, cfg->hbm_budget_bytes);
     if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc of the serving arena");
     s->arena.reset(cfg->hbm_budget_bytes);
-    e = cudaMalloc(&s->slot_dev, kSlots * kSlotBytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->slot_host, kSlots * kSlotBytes);
+    e = cudaMalloc(&s->desc_dev, kDescBytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->desc_host, kDescBytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking);
     for (int i = 0; i < cfg->n_streams && e == cudaSuccess; ++i) {
@@ -345,13 +411,15 @@ extern "C" sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out)
         if (e == cudaSuccess) s->s_comp.push_back(st);
     }
     if (e != cudaSuccess) {
+        for (auto st : s->s_comp) cudaStreamDestroy(st);
+        if (s->s_h2d) cudaStreamDestroy(s->s_h2d);
+        if (s->s_d2h) cudaStreamDestroy(s->s_d2h);
         cudaFree(s->arena_base);
-        cudaFree(s->slot_dev);
-        cudaFreeHost(s->slot_host);
+        cudaFree(s->desc_dev);
+        cudaFreeHost(s->desc_host);
         return fail_cuda(e, "serving set-up");
     }
-    s->slot_busy.assign(kSlots, false);
-    s->inflight_per_stream.assign(cfg->n_streams, 0);
+    s->desc_arena.reset(kDescBytes);
     sc5_server_s *raw = s.get();
     s->sched = std::thread([raw] { raw->scheduler_loop(); });
     s->compl_ = std::thread([raw] { raw->completion_loop(); });
@@ -374,6 +442,9 @@ extern "C" sc5_status serve_submit(sc5_server srv, const sc5_image *req, uint64_
         return fail(SC5_EINVAL, "scales must be finite and > 0");
     for (float t : im.k)
         if (!std::isfinite(t)) return fail(SC5_EINVAL, "taps must be finite");
+    if (!is_page_locked(im.in) || !is_page_locked(im.out))
+        return fail(SC5_EINVAL, "host buffers must be page-locked (cudaMallocHost or cudaHostRegister): copies "
+                                "from or to pageable memory block the scheduler");
     auto r = std::make_shared<Request>();
     r->img = im;
     r->in_bytes = static_cast<size_t>(srv->cfg.planes) * im.H * im.in_pitch * es;
@@ -451,14 +522,17 @@ extern "C" sc5_status serve_destroy(sc5_server srv)
     if (srv->sched.joinable()) srv->sched.join();
     if (srv->compl_.joinable()) srv->compl_.join();
     cudaSetDevice(srv->device);
+    for (auto st : srv->s_comp) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(srv->s_h2d);
     cudaStreamSynchronize(srv->s_d2h);
     for (auto st : srv->s_comp) cudaStreamDestroy(st);
     cudaStreamDestroy(srv->s_h2d);
     cudaStreamDestroy(srv->s_d2h);
-    for (auto e : srv->event_pool) cudaEventDestroy(e);
+    for (auto e : srv->plain_events) cudaEventDestroy(e);
+    for (auto e : srv->blocking_events) cudaEventDestroy(e);
     cudaFree(srv->arena_base);
-    cudaFree(srv->slot_dev);
-    cudaFreeHost(srv->slot_host);
+    cudaFree(srv->desc_dev);
+    cudaFreeHost(srv->desc_host);
     delete srv;
     return SC5_OK;
 }

@@ -431,6 +431,16 @@ class Server:
         _check(st, "serve_submit")
         return t.value
 
+    def submit_image(self, img) -> int | None:
+        """Queue a request given as a prepared ``Image`` structure (e.g. one
+        element of ``make_images``); None when the server pushes back."""
+        t = c_uint64()
+        st = load().serve_submit(self._h, byref(img), byref(t))
+        if st == EAGAIN:
+            return None
+        _check(st, "serve_submit")
+        return t.value
+
     def poll(self, ticket: int, timeout_us: int = -1) -> float | None:
         """Latency in microseconds once done; None if not done within the timeout."""
         lat = c_double()

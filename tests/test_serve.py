@@ -220,6 +220,15 @@ def test_refusals(sc5):
         with pytest.raises(sc5.Sepconv5Error) as e:
             srv.submit(r)
         assert e.value.status == sc5.EINVAL, key
+    # pageable host buffers are refused: their copies would block the scheduler
+    r, _ = _request(3, 64, 64, "bf16")
+    for key in ("in", "out"):
+        q = dict(r)
+        q[key] = r[key].clone()  # a plain (pageable) CPU tensor
+        assert not q[key].is_pinned()
+        with pytest.raises(sc5.Sepconv5Error) as e:
+            srv.submit(q)
+        assert e.value.status == sc5.EINVAL and "page-locked" in str(e.value), key
     with pytest.raises(sc5.Sepconv5Error) as e:
         srv.poll(123456, 0)
     assert e.value.status == sc5.ENOTFOUND
