@@ -229,6 +229,18 @@ def oracle_sample(A: np.ndarray, k: np.ndarray, target_s: float = 10.0) -> dict:
                       f"output pixels), FP64 direct Eq. 1, one thread, {dt:.1f} s"}
 
 
+def cpu_two_pass_sample(A: np.ndarray, k: np.ndarray) -> dict:
+    """The FP32 two-pass form with OpenMP on every host core (Listing 1's loop
+    structure, horizontal pass over all rows) on the whole image: median of 5
+    calls after a warm-up; 3-plane Mpix/s."""
+    import cpu_baseline
+    dt = cpu_baseline.time_two_pass(A, k, reps=5)
+    return {"value": round(H * W / dt / 1e6, 1), "unit": "Mpix/s", "ms_per_image": round(dt * 1e3, 2),
+            "cores": cpu_baseline.threads(), "nproc": os.cpu_count(), "cpu": cpu_baseline.cpu_model(),
+            "kind": "fp32 two-pass, OpenMP", "flags": " ".join(cpu_baseline.FLAGS),
+            "sample": f"the whole {P}x{H}x{W} image, median of 5 calls"}
+
+
 def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
     """Copy-only times for the offload bytes: host->device alone,
     device->host alone, and both at once on two streams."""
@@ -462,7 +474,7 @@ def leg_serve(sc5, synth, n_req, link=None):
     continuous batching against FP32 with one launch per request, at 0.5x,
     0.8x and 0.95x of the measured saturation request rate of the BF16
     server.  Latency = completion of the result's copy to the host minus the
-    request's scheduled arrival.  Pinned buffers: 32 outputs per size class."""
+    request's scheduled arrival.  Pinned buffers: 8 outputs per size class."""
     import torch
     sizes = synth.SERVE_SIZES
     out = {"workload": f"{n_req} requests per load, sizes {sizes} (H, W), Poisson arrivals",
@@ -481,13 +493,14 @@ def leg_serve(sc5, synth, n_req, link=None):
         return pool
 
     def run(dtype, merge, rate, n, pool, seed):
-        """One thread submits every request at its scheduled arrival time.
-        Request j of size class c writes output buffer j mod n_buf of that
-        class; before reusing a buffer the thread polls the ticket that last
-        wrote it.  The requests (sc5_image structures) are built before the
-        clock starts, so the thread does no marshalling in the loop, and the
-        server's own clock gives each latency (submit to result on the host),
-        to which the submission's lateness against its arrival time is added."""
+        """One thread submits every request at its scheduled arrival time and
+        polls the tickets once all are submitted.  The requests (sc5_image
+        structures) are built before the clock starts, so the loop does no
+        marshalling; the outputs of a size class rotate over its pinned
+        buffers without waiting (the benchmark does not read them), so a
+        client-side buffer never holds a submission back.  The server's own
+        clock gives each latency (submit to result on the host), to which the
+        submission's lateness against its arrival time is added."""
         srv = sc5.Server(hbm_budget_bytes=16 << 30, dtype=dtype, max_inflight=64, n_streams=2, merge=merge,
                          max_merge=8 if merge else 0)
         stream_ = synth.serve_stream(seed, n, rate) if rate else [(0.0, c, s) for (_, c, s) in synth.serve_stream(seed, n, 1.0)]
@@ -500,23 +513,9 @@ def leg_serve(sc5, synth, n_req, link=None):
                          "out_pitch": w - 4, "k": synth.kernel_normalised(kseed)})
             used[ci] += 1
         arr = sc5.make_images(reqs)
-        holder = [[None] * n_buf for _ in pool]  # (ticket, arrival, submit time) of the buffer's last user
-        lat = [[] for _ in pool]
-        late = []
-
-        def retire(item, ci):
-            tk, t_arr, t_sub = item
-            l_srv = srv.poll(tk, -1)
-            lat[ci].append(t_sub + l_srv * 1e-6 - t_arr)
-
-        count = [0] * len(pool)
+        tickets, late = [], []
         t_start = time.perf_counter()
         for j, (t_arr, ci, _) in enumerate(stream_):
-            slot = count[ci] % n_buf
-            count[ci] += 1
-            if holder[ci][slot] is not None:
-                retire(holder[ci][slot], ci)
-                holder[ci][slot] = None
             target = t_start + t_arr
             while True:
                 now = time.perf_counter()
@@ -530,11 +529,10 @@ def leg_serve(sc5, synth, n_req, link=None):
                 time.sleep(1e-4)
                 tk = srv.submit_image(arr[j])
             late.append(t_sub - target)
-            holder[ci][slot] = (tk, target, t_sub)
-        for ci in range(len(pool)):
-            for item in holder[ci]:
-                if item is not None:
-                    retire(item, ci)
+            tickets.append((tk, target, t_sub, ci))
+        lat = [[] for _ in pool]
+        for tk, target, t_sub, ci in tickets:
+            lat[ci].append(t_sub + srv.poll(tk, -1) * 1e-6 - target)
         wall = time.perf_counter() - t_start
         st = srv.stats()
         srv.close()
@@ -552,12 +550,7 @@ def leg_serve(sc5, synth, n_req, link=None):
                              for ph in ("queue", "stage", "run") for q in (50, 99)}}
         return res
 
-    # the submitting thread waits for arrival times with the interpreter lock
-    # held for at most ~100 us at a time; a short switch interval lets the
-    # pollers take it back promptly
-    old_switch = sys.getswitchinterval()
-    sys.setswitchinterval(1e-4)
-    pool_bf = make_pool("bf16", 32)
+    pool_bf = make_pool("bf16", 8)
     sat = run("bf16", True, 0.0, min(n_req, 2000), pool_bf, 11)
     rate_sat = sat["achieved_req_s"]
     # the link ceiling of this mix: each request's input crosses host->device
@@ -570,13 +563,12 @@ def leg_serve(sc5, synth, n_req, link=None):
         sat["link_ceiling_req_s"] = round(both * 1e9 / bytes_per_req, 1)
         sat["frac_of_link"] = round(rate_sat * bytes_per_req / (both * 1e9), 4)
     out["saturation_bf16_merged"] = sat
-    pool_f32 = make_pool("f32", 32)
+    pool_f32 = make_pool("f32", 8)
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
         out[f"load_{frac}"] = {"bf16_merged": run("bf16", True, rate, n_req, pool_bf, 20 + int(frac * 100)),
                                "f32_per_request": run("f32", False, rate, n_req, pool_f32, 20 + int(frac * 100))}
     del pool_bf, pool_f32
-    sys.setswitchinterval(old_switch)
     return out
 
 
@@ -874,6 +866,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         cpu = oracle_sample(A, k)
+        cpu["fp32_two_pass_openmp"] = cpu_two_pass_sample(A, k)
     plan.close()
     del A_host, out_host
     legs = [] if args.no_extras or rank != 0 else [x.strip() for x in args.legs.split(",") if x.strip()]

@@ -115,13 +115,17 @@ static sc5_status encode_image_map(CUtensorMap *m, int dtype, const void *base, 
     return SC5_OK;
 }
 
-// Columns of the TMA box: the tile plus the taps-1 halo, rounded up to 16
-// bytes and to the last lane's 4-element loads (as fused_box_w in the kernel).
+// Columns of one TMA box (as fused_box_w in the kernel): the 128 columns a
+// box covers (a 256-wide tile is two boxes) plus the taps-1 halo, rounded up
+// to 16 bytes and to the last lane's whole 4-element loads (4 output columns
+// per lane in 128-wide tiles, 8 in 256-wide ones).
 static int box_w_for(int dtype, int tile_w, int taps = kTaps)
 {
     const int es = dtype_bytes(dtype);
-    const int row_elems = (taps + 6) / 4 * 4;
-    const int need = std::max(tile_w + taps - 1, tile_w - 4 + row_elems);
+    const int cols = tile_w / 32;
+    const int cover = std::min(tile_w, 128);
+    const int row_elems = (cols + taps - 1 + 3) / 4 * 4;
+    const int need = std::max(cover + taps - 1, cover - cols + row_elems);
     return (need * es + 15) / 16 * 16 / es;
 }
 

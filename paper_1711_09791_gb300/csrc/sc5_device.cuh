@@ -196,6 +196,15 @@ template <> struct Fmt<bf16_t> {
         a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xffff0000u);
         a[2] = __uint_as_float(u.y << 16); a[3] = __uint_as_float(u.y & 0xffff0000u);
     }
+    // p[0..7] with one 16-byte load (p aligned to 8 elements)
+    __device__ static __forceinline__ void load8a(const bf16_t *p, float *a)
+    {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xffff0000u);
+        a[2] = __uint_as_float(u.y << 16); a[3] = __uint_as_float(u.y & 0xffff0000u);
+        a[4] = __uint_as_float(u.z << 16); a[5] = __uint_as_float(u.z & 0xffff0000u);
+        a[6] = __uint_as_float(u.w << 16); a[7] = __uint_as_float(u.w & 0xffff0000u);
+    }
     __device__ static __forceinline__ float load1(const bf16_t *p) { return bf16_bits_to_f32(p->v); }
     __device__ static __forceinline__ void store4(bf16_t *p, const float (&r)[4])
     {
@@ -223,6 +232,15 @@ template <> struct Fmt<f16_t> {
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
         f16x2_to_f32(u.x, a[0], a[1]);
         f16x2_to_f32(u.y, a[2], a[3]);
+    }
+    // p[0..7] with one 16-byte load (p aligned to 8 elements)
+    __device__ static __forceinline__ void load8a(const f16_t *p, float *a)
+    {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        f16x2_to_f32(u.x, a[0], a[1]);
+        f16x2_to_f32(u.y, a[2], a[3]);
+        f16x2_to_f32(u.z, a[4], a[5]);
+        f16x2_to_f32(u.w, a[6], a[7]);
     }
     __device__ static __forceinline__ float load1(const f16_t *p)
     {
@@ -256,6 +274,15 @@ template <> struct Fmt<fp8e4m3_t> {
         const uint32_t u = *reinterpret_cast<const uint32_t *>(p);
         e4m3x2_to_f32(u & 0xffffu, a[0], a[1]);
         e4m3x2_to_f32(u >> 16, a[2], a[3]);
+    }
+    // p[0..7] with one 8-byte load (p aligned to 8 elements)
+    __device__ static __forceinline__ void load8a(const fp8e4m3_t *p, float *a)
+    {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        e4m3x2_to_f32(u.x & 0xffffu, a[0], a[1]);
+        e4m3x2_to_f32(u.x >> 16, a[2], a[3]);
+        e4m3x2_to_f32(u.y & 0xffffu, a[4], a[5]);
+        e4m3x2_to_f32(u.y >> 16, a[6], a[7]);
     }
     __device__ static __forceinline__ float load1(const fp8e4m3_t *p)
     {

@@ -15,6 +15,13 @@ namespace sc5 {
         make_entry<TI, TO, 32, 128, 2, 12>(),                   \
         make_entry<TI, TO, 240, 128, 8, 4>(),                   \
         make_entry<TI, TO, 120, 128, 4, 6>(),                   \
+        /* 256-wide tiles: 8 output columns per lane */         \
+        make_entry<TI, TO, 128, 256, 16, 2>(),                  \
+        make_entry<TI, TO, 64, 256, 16, 3>(),                   \
+        make_entry<TI, TO, 64, 256, 8, 4>(),                    \
+        make_entry<TI, TO, 96, 256, 16, 3>(),                   \
+        make_entry<TI, TO, 32, 256, 8, 6>(),                    \
+        make_entry<TI, TO, 48, 256, 16, 4>(),                   \
     }
 
 int fused_entries_fp8(int out_dtype, const FusedEntry **out)

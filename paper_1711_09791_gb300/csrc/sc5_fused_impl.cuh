@@ -30,28 +30,42 @@ namespace sc5 {
 constexpr uint64_t kWaitLimitNs = 1000ull * 1000ull * 1000ull;  // 1 s per wait
 constexpr uint64_t kDrainLimitNs = 100ull * 1000ull * 1000ull;  // 0.1 s after an error
 
-// Elements of one input row a lane widens: its 4 columns plus the TAPS-1
+// Elements of one input row a lane widens: its COLS columns plus the TAPS-1
 // halo, rounded up to whole 4-element loads.
-template <int TAPS>
+template <int TAPS, int COLS = kColsPerThread>
 __host__ __device__ constexpr int row_elems()
 {
-    return (TAPS + 3 + 3) / 4 * 4;
+    return (COLS + TAPS - 1 + 3) / 4 * 4;
 }
 
-template <class TIn, int TAPS = kTaps>
+// Columns of one TMA box.  A tile 128 columns wide (4 output columns per
+// lane) is one box; a tile 256 wide (8 per lane) is two boxes, each covering
+// 128 output columns, because a box is at most 256 elements wide.  A box
+// holds its columns plus the TAPS-1 halo, rounded up so that a box row is a
+// multiple of 16 bytes and wide enough for the last lane's loads.
+template <class TIn, int TAPS = kTaps, int COLS = kColsPerThread>
 __host__ __device__ constexpr int fused_box_w(int tw)
 {
-    // TW + TAPS - 1 columns rounded up so that a box row is a multiple of 16
-    // bytes, and wide enough for the last lane's loads
     constexpr int es = Fmt<TIn>::bytes;
-    const int need = (tw + TAPS - 1) > (tw - 4 + row_elems<TAPS>()) ? (tw + TAPS - 1) : (tw - 4 + row_elems<TAPS>());
+    const int cover = tw > 128 ? 128 : tw;
+    const int need = (cover + TAPS - 1) > (cover - COLS + row_elems<TAPS, COLS>())
+                         ? (cover + TAPS - 1)
+                         : (cover - COLS + row_elems<TAPS, COLS>());
     return (need * es + 15) / 16 * 16 / es;
+}
+
+// Bytes of one box in shared memory (a multiple of 128) and of one stage
+// (all boxes of a tile).
+template <class TIn, int TH, int TW, int TAPS = kTaps>
+__host__ __device__ constexpr int fused_box_bytes()
+{
+    return (fused_box_w<TIn, TAPS, TW / 32>(TW) * (TH + TAPS - 1) * Fmt<TIn>::bytes + 127) / 128 * 128;
 }
 
 template <class TIn, int TH, int TW, int TAPS = kTaps>
 __host__ __device__ constexpr int fused_stage_bytes()
 {
-    return (fused_box_w<TIn, TAPS>(TW) * (TH + TAPS - 1) * Fmt<TIn>::bytes + 127) / 128 * 128;
+    return (TW / 128) * fused_box_bytes<TIn, TH, TW, TAPS>();
 }
 
 // The input pairs of one row for the packed arithmetic.  Output columns are
@@ -164,6 +178,78 @@ __device__ __forceinline__ void conv_strip(const TIn *__restrict__ s, const uint
     }
 }
 
+// ---- 8 output columns per lane (256-wide tiles, 8/16-bit inputs) ----
+// A lane widens 12 stored values per input row for 8 outputs (4 + 8 halo
+// values shared by twice as many outputs as with 4 columns).  The pairs are
+// Q[m] = (a[m], a[m+4]), m = 0..7: output pair c holds columns c and c+4,
+// and tap t of its row pass multiplies Q[c+t].  Per element the arithmetic
+// is exactly conv_strip's, so both strip shapes give the same bits.
+template <class TIn>
+__device__ __forceinline__ void row_pairs8(const TIn *__restrict__ p, uint64_t (&Q)[8])
+{
+    float a[12];
+    Fmt<TIn>::load8a(p, a);
+    Fmt<TIn>::load4(p + 8, a + 8);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) Q[m] = pack2(a[m], a[m + 4]);
+}
+
+template <class TOut>
+__device__ __forceinline__ void store_row8(const uint64_t (&v2)[4], uint64_t os2, bool scaled, TOut *dst,
+                                           int cols_valid, bool vec)
+{
+    float lo[4], hi[4];  // columns 0..3 and 4..7
+#pragma unroll
+    for (int c = 0; c < 4; ++c) unpack2(scaled ? mul2(v2[c], os2) : v2[c], lo[c], hi[c]);
+    if (vec && cols_valid == 8) {
+        Fmt<TOut>::store4(dst, lo);
+        Fmt<TOut>::store4(dst + 4, hi);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < cols_valid) Fmt<TOut>::store1(dst + c, c < 4 ? lo[c] : hi[c - 4]);
+    }
+}
+
+// One lane's strip of R output rows x 8 output columns, separable form.
+template <class TIn, class TOut, int R, int BW, bool FULL = false>
+__device__ __forceinline__ void conv_strip8(const TIn *__restrict__ s, const uint64_t (&kk)[kTaps], uint64_t os2,
+                                            bool scaled, TOut *__restrict__ out, int64_t out_pitch,
+                                            int rows_valid, int cols_valid, bool vec)
+{
+    static_assert(Fmt<TIn>::kStride2, "8 columns per lane are built for 8/16-bit inputs");
+    if constexpr (FULL) {
+        rows_valid = R;
+        cols_valid = 8;
+        vec = true;
+    }
+    uint64_t acc[R][4];
+#pragma unroll
+    for (int r = 0; r < R + kTaps - 1; ++r) {
+        uint64_t Q[8];
+        row_pairs8<TIn>(s + r * BW, Q);
+        uint64_t h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) h[c] = mul2(kk[0], Q[c]);
+#pragma unroll
+        for (int t = 1; t < kTaps; ++t)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h[c] = fma2(kk[t], Q[c + t], h[c]);
+        // input row r carries tap t = r - o of output row o
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+            const int o = r - t;
+            if (o >= 0 && o < R) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[o][c] = (t == 0) ? mul2(kk[0], h[c]) : fma2(kk[t], h[c], acc[o][c]);
+            }
+        }
+        const int o = r - (kTaps - 1);  // output row o has all its taps now
+        if (o >= 0 && o < rows_valid)
+            store_row8<TOut>(acc[o], os2, scaled, out + static_cast<int64_t>(o) * out_pitch, cols_valid, vec);
+    }
+}
+
 // The direct form's strip (sc5_fused_direct_strip.cuh) uses row_pairs and
 // store_row above.
 #include "sc5_fused_direct_strip.cuh"
@@ -184,25 +270,33 @@ __host__ __device__ constexpr bool fast_strips()
 {
     return sizeof(TIn) < 4 && (sizeof(TOut) < 4 || !BATCH);
 }
-template <class TIn, class TOut, int TH, int R, int TAPS>
+// 8-column strips: as many CTAs per SM as 18 warps make (about 113-146 registers;
+// fully unrolled, the strip otherwise holds up to ~190 to hoist its loads).
+template <class TIn, class TOut, int TH, int R, int TAPS, int COLS = kColsPerThread>
 __host__ __device__ constexpr int min_ctas_per_sm()
 {
+    if constexpr (COLS != kColsPerThread)
+        return 576 / (32 * (TH / R + 1)) > 1 ? 576 / (32 * (TH / R + 1)) : 1;
     return (sizeof(TIn) < 4 && sizeof(TOut) < 4 && TH / R + 1 <= 9 && TAPS <= 7) ? 3 : 1;
 }
 
 template <class TIn, class TOut, int TH, int TW, int R, int S, bool BATCH, bool DIRECT = false, int TAPS = kTaps>
-__global__ void __launch_bounds__(32 * (TH / R + 1), (min_ctas_per_sm<TIn, TOut, TH, R, TAPS>()))
+__global__ void __launch_bounds__(32 * (TH / R + 1), (min_ctas_per_sm<TIn, TOut, TH, R, TAPS, TW / 32>()))
 fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__ descs,
              const TileRec *__restrict__ tiles, int64_t ntiles, int *status)
 {
-    static_assert(TW == 32 * kColsPerThread, "one warp spans the tile width");
+    constexpr int COLS = TW / 32;                    // output columns per lane
+    constexpr int NBOX = TW / 128;                   // TMA boxes per tile
+    static_assert(TW == 128 || (TW == 256 && TAPS == kTaps && !DIRECT && Fmt<TIn>::kStride2),
+                  "one warp spans the tile width: 4 columns per lane, or 8 for 8/16-bit inputs");
     static_assert(TH % R == 0, "rows per thread must divide the tile height");
     static_assert(TAPS % 2 == 1 && TAPS <= kMaxTaps, "odd width up to kMaxTaps");
     static_assert(!DIRECT || TAPS == kTaps, "the direct form is built for width 5");
     constexpr int NC = TH / R;                       // consumer warps
-    constexpr int BW = fused_box_w<TIn, TAPS>(TW);
+    constexpr int BW = fused_box_w<TIn, TAPS, COLS>(TW);
+    constexpr int BOXB = fused_box_bytes<TIn, TH, TW, TAPS>();
     constexpr int STAGE = fused_stage_bytes<TIn, TH, TW, TAPS>();
-    constexpr uint32_t TX = BW * (TH + TAPS - 1) * Fmt<TIn>::bytes;
+    constexpr uint32_t TX = NBOX * BW * (TH + TAPS - 1) * Fmt<TIn>::bytes;
 
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S];
@@ -250,7 +344,9 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             }
             info[s] = rec;
             mbar_arrive_expect_tx(&full[s], TX);
-            tma_load_3d(smem + s * STAGE, m, &full[s], rec.tx * TW, rec.ty * TH, rec.plane);
+#pragma unroll
+            for (int b = 0; b < NBOX; ++b)  // x is a multiple of 128 elements: 16-byte aligned
+                tma_load_3d(smem + s * STAGE + b * BOXB, m, &full[s], rec.tx * TW + b * 128, rec.ty * TH, rec.plane);
             ++issued;
             if (++s == S) {
                 s = 0;
@@ -303,12 +399,15 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         const TileRec rec = info[s];
         if (BATCH) load_desc(descs[rec.img]);
         const int ry0 = rec.ty * TH + warp * R;
-        const int cx = rec.tx * TW + lane * kColsPerThread;
+        const int cx = rec.tx * TW + lane * COLS;
         const int rows_valid = min(R, Hv - ry0);
-        const int cols_valid = min(kColsPerThread, Wv - cx);
+        const int cols_valid = min(COLS, Wv - cx);
         if (rows_valid > 0 && cols_valid > 0) {
-            const TIn *src = reinterpret_cast<const TIn *>(smem + s * STAGE) +
-                             (warp * R) * BW + lane * kColsPerThread;
+            // lanes 0-15 of a 256-wide tile read the first box, lanes 16-31 the second
+            const int box = NBOX == 2 ? (lane >> 4) : 0;
+            const int bl = NBOX == 2 ? (lane & 15) : lane;
+            const TIn *src = reinterpret_cast<const TIn *>(smem + s * STAGE + box * BOXB) + (warp * R) * BW +
+                             bl * COLS;
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
             if constexpr (DIRECT) {
@@ -318,6 +417,12 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
                 else
                     conv_strip_direct<TIn, TOut, R, BW, false>(src, KK, os2, scaled, dst, out_pitch, rows_valid,
                                                                cols_valid, vec);
+            } else if constexpr (COLS == 8) {
+                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == COLS && vec)
+                    conv_strip8<TIn, TOut, R, BW, true>(src, kk, os2, scaled, dst, out_pitch, R, COLS, true);
+                else
+                    conv_strip8<TIn, TOut, R, BW, false>(src, kk, os2, scaled, dst, out_pitch, rows_valid,
+                                                         cols_valid, vec);
             } else {
                 if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
                     conv_strip<TIn, TOut, R, BW, TAPS, true>(src, kk, os2, scaled, dst, out_pitch, R,

@@ -33,7 +33,10 @@ def test_fused_configs_listed(sc5):
     for pair in [("f32", "f32"), ("bf16", "bf16"), ("bf16", "f32"), ("f16", "f16"), ("f16", "f32"),
                  ("fp8e4m3", "fp8e4m3"), ("fp8e4m3", "f32")]:
         cfgs = sc5.fused_configs(*pair)
-        assert cfgs and all(tw == 128 and th % 8 == 0 and 32 <= th + 4 <= 256 and st >= 2 for th, tw, st in cfgs)
+        # 128-wide tiles for every pair; 256-wide ones (8 columns per lane) for 8/16-bit inputs
+        widths = (128,) if pair[0] == "f32" else (128, 256)
+        assert cfgs and all(tw in widths and th % 8 == 0 and 32 <= th + 4 <= 256 and st >= 2 for th, tw, st in cfgs)
+        assert cfgs[0][1] == 128 or pair[0] != "f32"
         # a plan selects a shape by (tile_h, tile_w, stages): every triple must be unique
         assert len(set(cfgs)) == len(cfgs)
     with pytest.raises(sc5.Sepconv5Error):

@@ -99,3 +99,42 @@ def test_every_narrow_shape(sc5, in_dtype, out_dtype):
         assert U.max_abs(dec, ref) <= U.FP32_TOL
     else:
         assert np.all(np.abs(dec - ref) <= U.stored_tolerance(ref, out_dtype, out_scale, U.FP32_TOL))
+
+
+BATCH_SHAPES = [(300, 517), (67, 259), (130, 133), (5, 5), (64, 1030), (261, 77)]
+
+
+@pytest.mark.parametrize("in_dtype,out_dtype", NARROW_PAIRS)
+def test_every_narrow_shape_in_a_batch(sc5, in_dtype, out_dtype):
+    """The work-list kernel with every compiled shape of a pair (the tuner may
+    pick any of them for a batch or a merged serving launch), on ragged
+    images of several tile rows and columns, each image bitwise equal to its
+    two-pass result (checked against the oracle above)."""
+    import torch
+    imgs, twos = [], []
+    for i, (H, W) in enumerate(BATCH_SHAPES):
+        x = synth.image(60 + i, H, W)
+        scale = synth.fp8_scale(x) if in_dtype == "fp8e4m3" else 1.0
+        codes = synth.to_storage(x, in_dtype, scale)
+        pitch = U.pitch_for(W, in_dtype)
+        padded = np.zeros((3, H, pitch), codes.dtype)
+        padded[:, :, :W] = codes
+        k = synth.kernel_normalised(60 + i)
+        out_scale = 1.0 if out_dtype == "f32" else scale
+        A_dev = U.to_dev(padded)
+        twos.append(_run(sc5, A_dev, H, W, pitch, k, "two_pass", in_dtype, out_dtype, scale, out_scale))
+        op = U.pitch_for(W - 4, out_dtype)
+        imgs.append({"in": A_dev, "out": U.empty_dev((3, H - 4, op), out_dtype), "H": H, "W": W, "in_pitch": pitch,
+                     "out_pitch": op, "k": k, "in_scale": scale, "out_scale": out_scale})
+    for (th, tw, st) in sc5.fused_configs(in_dtype, out_dtype):
+        for im in imgs:
+            im["out"].copy_(U.empty_dev(tuple(im["out"].shape), out_dtype))
+        plan = sc5.Plan(3, 64, 64, in_dtype=in_dtype, out_dtype=out_dtype, tile_h=th, tile_w=tw, stages=st)
+        plan.run_batch(imgs)
+        torch.cuda.synchronize()
+        assert sc5.device_status() == 0
+        plan.close()
+        for im, two in zip(imgs, twos):
+            res = U.from_dev(im["out"], out_dtype)
+            assert U.sentinel_intact(res[:, :, im["W"] - 4:], out_dtype), (th, tw, st)
+            assert np.array_equal(res[:, :, :im["W"] - 4], two), (th, tw, st, im["H"], im["W"])
