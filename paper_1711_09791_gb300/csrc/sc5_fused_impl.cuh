@@ -259,6 +259,19 @@ __device__ __forceinline__ void record_error(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// The fields of a batch tile's image that the consumers use, copied from
+// the image's descriptor in global memory by the producer into a
+// shared-memory slot of the tile's stage, so that consumers start a tile
+// without a global-memory round trip.
+template <int TAPS>
+struct StageDesc {
+    void *out;
+    int64_t out_pitch, out_plane;
+    int32_t Hv, Wv, vec;
+    float oscale;
+    float k[TAPS];
+};
+
 // Which strip code a kernel instance runs, fixed per storage-format pair by
 // measurement on 3x8192x8192 images and the 256-image batch.  FP32 input is
 // HBM-bound: guarded strips only.  8/16-bit input is issue-bound: interior strips
@@ -302,6 +315,8 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
     __shared__ __align__(8) uint64_t full[S];
     __shared__ __align__(8) uint64_t empty[S];
     __shared__ TileRec info[S];
+    constexpr bool kStaged = BATCH && !DIRECT;  // image fields staged per tile by the producer
+    __shared__ StageDesc<TAPS> sdesc[kStaged ? S : 1];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -332,7 +347,20 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             const CUtensorMap *m;
             if (BATCH) {
                 rec = tiles[t];
-                m = &descs[rec.img].tmap;
+                const ImgDesc &d = descs[rec.img];
+                m = &d.tmap;
+                if constexpr (kStaged) {
+                    StageDesc<TAPS> &sd = sdesc[s];
+                    sd.out = d.out;
+                    sd.out_pitch = d.out_pitch;
+                    sd.out_plane = d.out_plane;
+                    sd.Hv = d.Hv;
+                    sd.Wv = d.Wv;
+                    sd.vec = d.vec;
+                    sd.oscale = d.oscale;
+#pragma unroll
+                    for (int q = 0; q < TAPS; ++q) sd.k[q] = d.k[q];
+                }
             } else {
                 const int64_t per_plane = static_cast<int64_t>(single.tiles_x) * single.tiles_y;
                 rec.img = 0;
@@ -387,6 +415,18 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         Wv = d.Wv;
         vec = d.vec != 0;
     };
+    auto load_staged = [&](const StageDesc<TAPS> &d) {
+#pragma unroll
+        for (int q = 0; q < TAPS; ++q) kk[q] = pack2(d.k[q], d.k[q]);
+        os2 = pack2(d.oscale, d.oscale);
+        scaled = d.oscale != 1.f;
+        out_base = static_cast<unsigned char *>(d.out);
+        out_pitch = d.out_pitch;
+        out_plane = d.out_plane;
+        Hv = d.Hv;
+        Wv = d.Wv;
+        vec = d.vec != 0;
+    };
     if (!BATCH) load_desc(single);
     int s = 0;
     uint32_t phase = 0;
@@ -397,7 +437,10 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             return;
         }
         const TileRec rec = info[s];
-        if (BATCH) load_desc(descs[rec.img]);
+        if constexpr (kStaged)
+            load_staged(sdesc[s]);
+        else if constexpr (BATCH)
+            load_desc(descs[rec.img]);
         const int ry0 = rec.ty * TH + warp * R;
         const int cx = rec.tx * TW + lane * COLS;
         const int rows_valid = min(R, Hv - ry0);
