@@ -349,6 +349,8 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
                 rec = tiles[t];
                 const ImgDesc &d = descs[rec.img];
                 m = &d.tmap;
+                // the next tile's map: its descriptor fetch overlaps this tile's wait
+                if (t + gridDim.x < ntiles) prefetch_tmap(&descs[tiles[t + gridDim.x].img].tmap);
                 if constexpr (kStaged) {
                     StageDesc<TAPS> &sd = sdesc[s];
                     sd.out = d.out;
