@@ -353,7 +353,8 @@ void sc5_server_s::completion_loop()
             if (issued.empty()) break;  // the scheduler has finished and everything completed
             r = issued.front();
         }
-        // sleeps until the copy lands (blocking-sync event); outside the lock
+        // sleeps until the copy lands (blocking-sync event); outside the lock.
+        // (Spinning on cudaEventQuery instead measured no shorter tail.)
         const cudaError_t q = cudaEventSynchronize(r->done_ev);
         const auto now = Clock::now();
         {
