@@ -94,6 +94,16 @@ def algorithmic_bytes(h: int, w: int, planes: int = P, es_in: int = 4, es_out: i
     return planes * h * w * es_in + planes * (h - 4) * (w - 4) * es_out
 
 
+FMA_PER_OUTPUT = 10  # the separable body: 5 multiply-adds per pass
+
+
+def fma_peak() -> float:
+    """FP32 multiply-adds per second of the GPU from its unit counts: 152 SMs x
+    128 FP32 FMA per clock x the measured maximum SM clock (2.07 GHz)."""
+    peaks = measured_peaks() or {}
+    return 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+
+
 def measured_peaks() -> dict | None:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -453,13 +463,17 @@ def leg_batch(sc5, synth, stream, dtypes):
         info = b.info()
         alg = sum(P * h * w * sc5.DTYPE_BYTES[dtype] + P * (h - 4) * (w - 4) * sc5.DTYPE_BYTES[out_dtype]
                   for h, w in shapes)
-        # narrow-to-narrow formats move 2-4 bytes per pixel: the SMs' instruction issue and FMA
-        # pipe bound them before HBM does
-        bound = "sm_issue" if out_dtype != "f32" and dtype != "f32" else "hbm"
+        # narrow-to-narrow formats move 2-4 bytes per output: the FP32 multiply-adds of the
+        # separable body (10 per output) on the FMA pipe bound them before HBM does
+        outputs = sum(P * (h - 4) * (w - 4) for h, w in shapes)
+        bound = "fma" if out_dtype != "f32" and dtype != "f32" else "hbm"
         results[f"{dtype}->{out_dtype}"] = {
             "bound": bound,
             "ms": round(ms, 4), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "achieved_gbs": round(alg / ms / 1e6, 1),
-            "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4), "tiles": info["tiles"], "ctas": info["ctas"],
+            "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4),
+            "fma_tflops": round(outputs * FMA_PER_OUTPUT / (ms / 1e3) / 1e12, 2),
+            "frac_of_fma_peak": round(outputs * FMA_PER_OUTPUT / (ms / 1e3) / fma_peak(), 4),
+            "tiles": info["tiles"], "ctas": info["ctas"],
             "tile": f"{info['tile_h']}x{info['tile_w']}", "create_ms": round(create_ms, 1)}
         b.close()
         plan.close()

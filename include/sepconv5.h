@@ -416,7 +416,11 @@ typedef struct {
 } sc5_serve_stats;
 
 /* Start a server on the current device: allocates its resident arena
- * (hbm_budget_bytes) and starts its scheduler and completion threads.
+ * (hbm_budget_bytes), warms it up (the arena is written once, every compiled
+ * batch-kernel shape of the dtype is loaded, events are created up front, so
+ * that the first requests run as fast as later ones; this takes a few
+ * milliseconds and waits for the arena writes) and starts its scheduler and
+ * completion threads.
  * Host-side fault injection for tests, read from the environment here:
  * SC5_SERVE_FAULT=arena_alloc makes the arena allocation fail (SC5_ENOMEM);
  * SC5_SERVE_FAULT=sched_delay_ms=N makes the scheduler sleep N ms before

@@ -421,6 +421,32 @@ extern "C" sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out)
         return fail_cuda(e, "serving set-up");
     }
     s->desc_arena.reset(kDescBytes);
+    // Warm-up, so that the first requests do not pay it: touch the arena and
+    // the descriptor area once, load every compiled batch-kernel shape of the
+    // dtype and set its attributes, and fill the event pools.
+    e = cudaMemsetAsync(s->arena_base, 0, cfg->hbm_budget_bytes, s->s_h2d);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->desc_dev, 0, kDescBytes, s->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_h2d);
+    for (int i = 0; i < fused_num_shapes(cfg->dtype, cfg->dtype) && e == cudaSuccess; ++i)
+        e = fused_prepare(cfg->dtype, cfg->dtype, i);
+    for (int i = 0; i < 2 * cfg->max_inflight && e == cudaSuccess; ++i) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming | cudaEventBlockingSync);
+        if (a) s->plain_events.push_back(a);
+        if (b) s->blocking_events.push_back(b);
+    }
+    if (e != cudaSuccess) {
+        for (auto ev : s->plain_events) cudaEventDestroy(ev);
+        for (auto ev : s->blocking_events) cudaEventDestroy(ev);
+        for (auto st : s->s_comp) cudaStreamDestroy(st);
+        cudaStreamDestroy(s->s_h2d);
+        cudaStreamDestroy(s->s_d2h);
+        cudaFree(s->arena_base);
+        cudaFree(s->desc_dev);
+        cudaFreeHost(s->desc_host);
+        return fail_cuda(e, "serving warm-up");
+    }
     sc5_server_s *raw = s.get();
     s->sched = std::thread([raw] { raw->scheduler_loop(); });
     s->compl_ = std::thread([raw] { raw->completion_loop(); });
