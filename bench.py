@@ -17,6 +17,10 @@ The second form times one configuration on its own and prints its JSON line
 
 Multi-GPU (launched by torchrun): every rank convolves its own image (no
 collective on the data path; weak scaling); the time is the max over ranks.
+With --split rows the ranks share one image instead: each convolves a band
+of its output rows, reading the band's 2-row halos from the source image, so
+there is still no exchange (strong scaling).  The end-to-end offload leg
+stays one whole image per rank in both modes.
 """
 from __future__ import annotations
 
@@ -56,6 +60,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="only the timed fused leg")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests per offered load")
     ap.add_argument("--legs", default="c1,c3,c4,paper,pyramid,c5", help="extra configs to run beside the headline")
+    ap.add_argument("--split", default="images", choices=["images", "rows"],
+                    help="N > 1: every rank convolves its own image (weak scaling), or a band of rows of one "
+                         "image with its halo read from the source (strong scaling)")
     ap.add_argument("--case", default=None,
                     help="time one configuration instead of the contract run (the command the ncu captures use): "
                          "comma-separated key=value with keys dtype, out, algo (fused|two_pass|direct|reduce), "
@@ -71,6 +78,16 @@ def parse():
 def rank_image_seed(rank: int) -> int:
     """Every rank convolves its own image (weak scaling, no data exchange)."""
     return SEED + rank
+
+
+def row_band(Hv: int, world: int, rank: int) -> tuple[int, int]:
+    """Output rows [r0, r1) of a rank's band when the VALID rows of one image
+    are split across ranks as evenly as possible.  The band reads input rows
+    [r0, r1 + 4): its 2-row halos come from the source image, so bands need
+    no exchange."""
+    base, extra = divmod(Hv, world)
+    r0 = rank * base + min(rank, extra)
+    return r0, r0 + base + (1 if rank < extra else 0)
 
 
 def reduce_max(x: float, world: int, device=None) -> float:
@@ -722,12 +739,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     sepconv5.load()
-    A = synth.image(rank_image_seed(rank), H, W)
+    rows = args.split == "rows"
+    A = synth.image(SEED if rows else rank_image_seed(rank), H, W)
     k = synth.kernel_normalised(SEED)
     A_dev = torch.from_numpy(A).to(dev)
     out = torch.empty((P, H - 4, W - 4), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     plan = sepconv5.Plan(P, H, W, W, W - 4, algo="fused")
+    # rows split: this rank's band of output rows, as views with the whole image's plane strides
+    r0, r1 = row_band(H - 4, world, rank) if rows else (0, H - 4)
+    band = sepconv5.Plan(P, r1 - r0 + 4, W, W, W - 4, in_plane_stride=H * W, out_plane_stride=(H - 4) * (W - 4))
+    band_in, band_out = A_dev[:, r0:, :], out[:, r0:, :]
 
     def barrier():
         if world > 1:
@@ -760,15 +782,21 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sampler = ClockSampler(smi_index)
     sampler.start()
     sampler.mark(0)
-    ms, launches = timed(lambda: plan.run(A_dev, out, k, stream=stream), args.steps, max(args.warmup, 3))
+    if rows:
+        ms, launches = timed(lambda: band.run(band_in, band_out, k, stream=stream), args.steps, max(args.warmup, 3))
+    else:
+        ms, launches = timed(lambda: plan.run(A_dev, out, k, stream=stream), args.steps, max(args.warmup, 3))
+    band.close()
     sampler.mark(1)
     clocks = sampler.stop()
     if sepconv5.device_status(stream) != 0:
         raise RuntimeError("a kernel reported a device error during the timed region")
 
-    alg = algorithmic_bytes(H, W)
+    # bytes of this rank's launch (its band when the rows are split)
+    alg = algorithmic_bytes(H, W) if not rows else P * (r1 - r0 + 4) * W * 4 + P * (r1 - r0) * (W - 4) * 4
     pixels = H * W
-    value = whole_job_value(world, pixels, ms)
+    # rows split: the ranks share one image, so the whole job is that image
+    value = whole_job_value(1 if rows else world, pixels, ms)
     peaks = measured_peaks()
     if peaks and peaks.get("hbm_gbs"):
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
@@ -909,8 +937,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": run_config(world),
+        "scaling": "strong" if rows else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": run_config(world, args.split),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
                      "peak_source": peak_src, "kernel": "fused_kernel<float,float> (single image)",
@@ -924,11 +952,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     return line
 
 
-def run_config(world: int) -> dict:
+def run_config(world: int, split: str = "images") -> dict:
     """The workload both arms report (the reference arm times the oracle on it)."""
     return {"workload": WORKLOAD, "planes": P, "H": H, "W": W, "seed": SEED, "border": "valid",
             "l2": "inputs larger than L2 (805 MB in, 804 MB out per step); no flush",
-            "parallelism": f"replicas x{world}"}
+            "parallelism": f"replicas x{world}" if split == "images" else f"row bands x{world}"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -953,8 +981,8 @@ def run_reference(args, rank: int, world: int):
     sample = f"{rows + 4} input rows x {W} cols x {P} planes per step ({rows} x {W - 4} output pixels), FP64 direct Eq. 1, one thread"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world,
             "steps": steps, "warmup": 3, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": run_config(world),
+            "scaling": "strong" if getattr(args, "split", "images") == "rows" else "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": run_config(world, getattr(args, "split", "images")),
             "cpu_baseline": {"value": round(value, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -1,7 +1,8 @@
 """The multi-process path of bench.py on CPU: two gloo ranks check the
 max-over-ranks timing, the whole-job value (all ranks' pixels over the
-slowest rank's time, weak scaling), distinct per-rank images, and that the
-reference arm runs on rank 0 alone."""
+slowest rank's time, weak scaling), distinct per-rank images, that the
+reference arm runs on rank 0 alone, and that the row bands of the strong-
+scaling split cover an image's output rows exactly once."""
 import os
 import socket
 
@@ -32,7 +33,10 @@ def _worker(rank, world, port, results):
         class A:
             steps, warmup = 1, 0
         ref = bench.run_reference(A(), rank, world) if rank != 0 else "skipped"
-        results[rank] = (mx, value, bench.rank_image_seed(rank), ref)
+        # rows split: the bands of all ranks cover the VALID rows exactly once
+        bands = [None] * world
+        dist.all_gather_object(bands, bench.row_band(8188, world, rank))
+        results[rank] = (mx, value, bench.rank_image_seed(rank), ref, bands)
     finally:
         dist.destroy_process_group()
 
@@ -48,3 +52,17 @@ def test_two_gloo_ranks():
     assert r[0][1] == pytest.approx(expect) and r[1][1] == pytest.approx(expect)
     assert r[0][2] != r[1][2]  # each rank has its own image
     assert r[1][3] is None  # the reference arm does no work on rank 1
+    bands = r[0][4]
+    assert bands == r[1][4] and bands[0][0] == 0 and bands[-1][1] == 8188
+    assert all(a[1] == b[0] and a[0] < a[1] for a, b in zip(bands, bands[1:] + [(8188, 8189)]))
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 7, 8])
+def test_row_bands_partition(world):
+    import bench
+    for hv in (1, 7, 8188, 8189):
+        bands = [bench.row_band(hv, world, r) for r in range(world)]
+        assert bands[0][0] == 0 and bands[-1][1] == hv
+        assert all(a[1] == b[0] for a, b in zip(bands, bands[1:]))
+        sizes = [b - a for a, b in bands]
+        assert max(sizes) - min(sizes) <= 1
