@@ -320,6 +320,45 @@ def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
             "both_2streams_gbs": round((nb_in + nb_out) / ts / 1e6, 1)}
 
 
+def link_stalls(seconds: float = 3.0, nbytes: int = 3 * 1076 * 1916 * 2) -> dict:
+    """Plain back-to-back copies of a 1920x1080 BF16 output in both directions
+    at once (no server involved) for a few seconds; the gaps between
+    consecutive copy completions on the device clock show how often, and for
+    how long, the CPU-GPU link stalls."""
+    import torch
+    hbuf = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(4)]
+    dbuf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dsrc = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_d, s_h = torch.cuda.Stream(), torch.cuda.Stream()
+    base = torch.cuda.Event(enable_timing=True)
+    base.record(s_d)
+    base.synchronize()
+    evs = {"d2h": [], "h2d": []}
+    t0, i = time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(16):
+            with torch.cuda.stream(s_d):
+                hbuf[i % 4].copy_(dsrc, non_blocking=True)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(s_d)
+                evs["d2h"].append(e)
+            with torch.cuda.stream(s_h):
+                dbuf.copy_(hbuf[(i + 2) % 4], non_blocking=True)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(s_h)
+                evs["h2d"].append(e)
+            i += 1
+        evs["h2d"][-1].synchronize()
+    torch.cuda.synchronize()
+    out = {"seconds": seconds, "copies_per_direction": i, "bytes_each": nbytes}
+    for kind, lst in evs.items():
+        ts = [base.elapsed_time(e) for e in lst]
+        gaps = sorted(b - a for a, b in zip(ts, ts[1:]))
+        out[kind] = {"median_gap_ms": round(gaps[len(gaps) // 2], 4), "max_gap_ms": round(gaps[-1], 3),
+                     "gaps_over_5ms": sum(g > 5.0 for g in gaps)}
+    return out
+
+
 # ------------------------------------------------------------------ other configs
 
 
@@ -597,6 +636,7 @@ def leg_serve(sc5, synth, n_req, link=None):
         sat["link_ceiling_req_s"] = round(both * 1e9 / bytes_per_req, 1)
         sat["frac_of_link"] = round(rate_sat * bytes_per_req / (both * 1e9), 4)
     out["saturation_bf16_merged"] = sat
+    out["link_stalls"] = link_stalls()
     pool_f32 = make_pool("f32", 8)
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
