@@ -486,9 +486,10 @@ def _batch_images(sc5, synth, dtype, shapes, x_dev, scales):
 
 def leg_batch(sc5, synth, stream, dtypes):
     """The 256-image batch (H, W log-uniform in [64, 4096]): one persistent
-    launch over the tile work-list, replayed from a CUDA graph, tile shape
-    from the autotuner and CTAs per SM timed on the batch itself when it is
-    created (ctas_per_sm = -1); FP32 and the stored formats."""
+    launch over the tile work-list, replayed from a CUDA graph, tile shape and
+    CTAs per SM timed on the batch itself when it is created (ctas_per_sm =
+    -2: every compiled shape at every feasible CTA count); FP32 and the stored
+    formats."""
     import torch
     shapes = synth.batch_shapes(3, 256)
     x_dev = [torch.from_numpy(synth.image(3000 + i, h, w)).cuda() for i, (h, w) in enumerate(shapes)]
@@ -511,7 +512,7 @@ def leg_batch(sc5, synth, stream, dtypes):
             if out_dtype == "f32":
                 im["out_scale"] = 1.0
             outs.append(o)
-        plan = sc5.Plan(P, 64, 64, in_dtype=dtype, out_dtype=out_dtype, ctas_per_sm=-1)
+        plan = sc5.Plan(P, 64, 64, in_dtype=dtype, out_dtype=out_dtype, ctas_per_sm=-2)
         t0 = time.perf_counter()
         b = sc5.Batch(plan, imgs)
         create_ms = (time.perf_counter() - t0) * 1e3

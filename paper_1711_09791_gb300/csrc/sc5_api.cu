@@ -1107,7 +1107,7 @@ struct sc5_batch_s {
 // one warm-up and three timed launches each on a private stream, median kept
 // (the launches write the batch's outputs, as its first replay would).
 static cudaError_t time_batch_ctas(int in_dtype, int out_dtype, int idx, unsigned char *ws, size_t toff,
-                                   int64_t ntiles, int *ctas)
+                                   int64_t ntiles, int *ctas, float *best_ms = nullptr)
 {
     const int maxc = fused_max_ctas_per_sm(in_dtype, out_dtype, idx);
     if (maxc < 1) return cudaErrorInvalidConfiguration;
@@ -1138,10 +1138,47 @@ static cudaError_t time_batch_ctas(int in_dtype, int out_dtype, int idx, unsigne
             *ctas = c;
         }
     }
+    if (best_ms) *best_ms = best;
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);
     if (s) cudaStreamDestroy(s);
     return e;
+}
+
+// Every compiled shape of the plan's dtype pair, each at every feasible CTA
+// count, timed on the batch itself (its own work-list per shape); the
+// fastest (shape index, CTAs per SM).  The timing launches write the
+// batch's outputs.
+static sc5_status time_batch_shapes(const sc5_plan_desc &d, int n, const sc5_image *imgs, int *idx, int *ctas)
+{
+    float best = 0.f;
+    int found = -1;
+    for (int i = 0; i < fused_num_shapes(d.in_dtype, d.out_dtype); ++i) {
+        FusedShape sh{};
+        fused_shape(d.in_dtype, d.out_dtype, i, &sh);
+        std::vector<unsigned char> blob;
+        int64_t ntiles = 0;
+        size_t toff = 0;
+        sc5_status st = build_batch(d, n, imgs, sh, &blob, &ntiles, &toff);
+        if (st != SC5_OK) return st;
+        unsigned char *ws = nullptr;
+        cudaError_t e = cudaMalloc(&ws, blob.size());
+        if (e == cudaSuccess) e = cudaMemcpy(ws, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = fused_prepare(d.in_dtype, d.out_dtype, i);
+        int c = 1;
+        float ms = 0.f;
+        if (e == cudaSuccess) e = time_batch_ctas(d.in_dtype, d.out_dtype, i, ws, toff, ntiles, &c, &ms);
+        cudaFree(ws);
+        if (e != cudaSuccess) return fail_cuda(e, "timing the batch's shapes");
+        if (found < 0 || ms < best) {
+            best = ms;
+            found = i;
+            *ctas = c;
+        }
+    }
+    if (found < 0) return fail(SC5_EINVAL, "no compiled shape for the dtype pair");
+    *idx = found;
+    return SC5_OK;
 }
 
 extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_image *imgs, sc5_batch *out)
@@ -1155,6 +1192,11 @@ extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_ima
     int idx = 0, ctas = 1;
     sc5_status st = batch_shape(p, n, imgs, &idx, &ctas);
     if (st != SC5_OK) return st;
+    const bool time_shapes = p->d.ctas_per_sm == -2 && !p->d.tile_h && !p->d.tile_w && !p->d.stages;
+    if (time_shapes) {
+        st = time_batch_shapes(p->d, n, imgs, &idx, &ctas);
+        if (st != SC5_OK) return st;
+    }
     sc5_batch b = new (std::nothrow) sc5_batch_s;
     if (!b) return fail(SC5_ENOMEM, "host allocation failed");
     cudaGetDevice(&b->device);
@@ -1169,7 +1211,7 @@ extern "C" sc5_status sepconv5_batch_create(sc5_plan p, int32_t n, const sc5_ima
     cudaError_t e = cudaMalloc(&b->ws, blob.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->ws, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = fused_prepare(p->d.in_dtype, p->d.out_dtype, idx);
-    if (e == cudaSuccess && p->d.ctas_per_sm < 0)
+    if (e == cudaSuccess && p->d.ctas_per_sm < 0 && !time_shapes)
         e = time_batch_ctas(p->d.in_dtype, p->d.out_dtype, idx, b->ws, toff, b->ntiles, &ctas);
     const int64_t cap = static_cast<int64_t>(num_sms()) * ctas;
     b->grid = static_cast<int>(std::max<int64_t>(1, std::min(b->ntiles, cap)));

@@ -149,8 +149,9 @@ def test_full_batch_every_pixel(batch_outputs):
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_batch_ctas_timed_on_create(dtype):
     """ctas_per_sm = -1: the batch times every feasible CTA count on itself at
-    creation; the outputs do not depend on the count (bitwise equal to an
-    explicit one CTA per SM) and the grid is a whole number of CTAs per SM."""
+    creation; -2: every compiled shape at every count.  The outputs do not
+    depend on either choice (bitwise equal to an explicit one CTA per SM) and
+    the grid is a whole number of CTAs per SM."""
     import torch
     from paper_1711_09791_gb300 import sepconv5 as sc5
     sc5.load()
@@ -158,7 +159,7 @@ def test_batch_ctas_timed_on_create(dtype):
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dtype]
     es = sc5.DTYPE_BYTES[dtype]
     runs = []
-    for ctas in (1, -1):
+    for ctas in (1, -1, -2):
         imgs = []
         for i, (h, w) in enumerate(shapes):
             x = torch.from_numpy(synth.image(5000 + i, h, w)).cuda()
@@ -179,5 +180,6 @@ def test_batch_ctas_timed_on_create(dtype):
         runs.append([im["out"].clone() for im in imgs])
         b.close()
         plan.close()
-    for a, c in zip(*runs):
-        assert torch.equal(a, c)
+    for run in runs[1:]:
+        for a, c in zip(runs[0], run):
+            assert torch.equal(a, c)
