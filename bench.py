@@ -637,7 +637,7 @@ def leg_serve(sc5, synth, n_req, link=None):
         sat["link_ceiling_req_s"] = round(both * 1e9 / bytes_per_req, 1)
         sat["frac_of_link"] = round(rate_sat * bytes_per_req / (both * 1e9), 4)
     out["saturation_bf16_merged"] = sat
-    out["link_stalls"] = link_stalls()
+    out["link_stalls"] = link_stalls(6.0)
     pool_f32 = make_pool("f32", 8)
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
