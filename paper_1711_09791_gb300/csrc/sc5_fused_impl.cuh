@@ -447,7 +447,13 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         const int cx = rec.tx * TW + lane * COLS;
         const int rows_valid = min(R, Hv - ry0);
         const int cols_valid = min(COLS, Wv - cx);
-        if (rows_valid > 0 && cols_valid > 0) {
+        const bool active = rows_valid > 0 && cols_valid > 0;
+        // The warp runs the guard-free strip only if every active lane's strip
+        // is interior: a warp with one edge lane then runs the guarded strip
+        // alone instead of both (both give the same values).
+        const bool interior = fast_strips<TIn, TOut, BATCH>() &&
+                              __all_sync(0xffffffffu, !active || (rows_valid == R && cols_valid == COLS && vec));
+        if (active) {
             // lanes 0-15 of a 256-wide tile read the first box, lanes 16-31 the second
             const int box = NBOX == 2 ? (lane >> 4) : 0;
             const int bl = NBOX == 2 ? (lane & 15) : lane;
@@ -456,20 +462,20 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
             if constexpr (DIRECT) {
-                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
+                if (interior)
                     conv_strip_direct<TIn, TOut, R, BW, true>(src, KK, os2, scaled, dst, out_pitch, R,
                                                               kColsPerThread, true);
                 else
                     conv_strip_direct<TIn, TOut, R, BW, false>(src, KK, os2, scaled, dst, out_pitch, rows_valid,
                                                                cols_valid, vec);
             } else if constexpr (COLS == 8) {
-                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == COLS && vec)
+                if (interior)
                     conv_strip8<TIn, TOut, R, BW, true>(src, kk, os2, scaled, dst, out_pitch, R, COLS, true);
                 else
                     conv_strip8<TIn, TOut, R, BW, false>(src, kk, os2, scaled, dst, out_pitch, rows_valid,
                                                          cols_valid, vec);
             } else {
-                if (fast_strips<TIn, TOut, BATCH>() && rows_valid == R && cols_valid == kColsPerThread && vec)
+                if (interior)
                     conv_strip<TIn, TOut, R, BW, TAPS, true>(src, kk, os2, scaled, dst, out_pitch, R,
                                                              kColsPerThread, true);
                 else
