@@ -14,11 +14,7 @@ namespace sc5 {
         make_entry<TI, TO, 64, 256, 8, 3>(),                    \
         make_entry<TI, TO, 96, 256, 16, 2>(),                   \
         make_entry<TI, TO, 32, 256, 8, 4>(),                    \
-        make_entry<TI, TO, 48, 256, 16, 3>(),                   \
-        /* 32 rows per lane: the row pass repeats on 4 of 36 rows */ \
-        make_entry<TI, TO, 96, 128, 32, 3>(),                   \
-        make_entry<TI, TO, 160, 128, 32, 2>(),                  \
-        make_entry<TI, TO, 192, 128, 32, 2>(),
+        make_entry<TI, TO, 48, 256, 16, 3>(),
 
 // The default shape runs 2 CTAs per SM when untuned: on 3x8192x8192 BF16 it
 // measured 0.131 ms there against 0.149-0.150 ms at 1 or 3.

@@ -22,10 +22,6 @@ namespace sc5 {
         make_entry<TI, TO, 96, 256, 16, 3>(),                   \
         make_entry<TI, TO, 32, 256, 8, 6>(),                    \
         make_entry<TI, TO, 48, 256, 16, 4>(),                   \
-        /* 32 rows per lane */                                  \
-        make_entry<TI, TO, 96, 128, 32, 4>(),                   \
-        make_entry<TI, TO, 160, 128, 32, 3>(),                  \
-        make_entry<TI, TO, 192, 128, 32, 3>(),                  \
     }
 
 int fused_entries_fp8(int out_dtype, const FusedEntry **out)
