@@ -66,9 +66,9 @@ def parse():
     ap.add_argument("--case", default=None,
                     help="time one configuration instead of the contract run (the command the ncu captures use): "
                          "comma-separated key=value with keys dtype, out, algo (fused|two_pass|direct|reduce), "
-                         "layout (planar|hwc), planes, H, W, tile (THxTWxSTAGES), ctas, batch (N > 0: the first N "
-                         "images of the 256-image batch as one graph-replayed launch); --steps timed launches "
-                         "after --warmup")
+                         "layout (planar|hwc), planes, H, W, tile (THxTWxSTAGES), ctas, taps (kernel width), opitch "
+                         "(output pitch in elements; 0: rows rounded to 16 bytes), batch (N > 0: the first N images "
+                         "of the 256-image batch as one graph-replayed launch); --steps timed launches after --warmup")
     return ap.parse_args()
 
 
@@ -653,12 +653,12 @@ def leg_serve(sc5, synth, n_req, link=None):
 def parse_case(spec: str) -> dict:
     """`--case` key=value list -> options (defaults: 3 x 8192 x 8192 FP32 fused, planar)."""
     c = {"dtype": "f32", "out": None, "algo": "fused", "layout": "planar", "planes": P, "H": H, "W": W,
-         "tile": "", "ctas": 0, "batch": 0}
+         "tile": "", "ctas": 0, "batch": 0, "taps": 5, "opitch": 0}
     for item in filter(None, (x.strip() for x in spec.split(","))):
         key, _, val = item.partition("=")
         if key not in c:
             raise SystemExit(f"--case: unknown key {key!r} (keys: {', '.join(c)})")
-        c[key] = int(val) if key in ("planes", "H", "W", "ctas", "batch") else val
+        c[key] = int(val) if key in ("planes", "H", "W", "ctas", "batch", "taps", "opitch") else val
     c["out"] = c["out"] or c["dtype"]
     return c
 
@@ -685,7 +685,8 @@ def run_case(args):
     th = tw = st = 0
     if c["tile"]:
         th, tw, st = (int(v) for v in c["tile"].split("x"))
-    Ho, Wo = sc5.reduce_dims(Hc, Wc) if c["algo"] == "reduce" else (Hc - 4, Wc - 4)
+    n = c["taps"]
+    Ho, Wo = sc5.reduce_dims(Hc, Wc) if c["algo"] == "reduce" else (Hc - n + 1, Wc - n + 1)
     if c["layout"] == "hwc":
         pitch = -(-3 * Wc * es // 16) * 16 // es
         opitch = -(-3 * Wo // 4) * 4
@@ -694,13 +695,17 @@ def run_case(args):
         out = torch.empty((Ho, opitch), dtype=tdt[odt], device="cuda")
     else:
         pitch = -(-Wc * es // 16) * 16 // es
-        opitch = -(-Wo * eo // 16) * 16 // eo
+        opitch = c["opitch"] or -(-Wo * eo // 16) * 16 // eo
         A = torch.zeros((Pc, Hc, pitch), dtype=tdt[dt], device="cuda")
         A[:, :, :Wc] = (x * scale).to(tdt[dt])
         out = torch.empty((Pc, Ho, opitch), dtype=tdt[odt], device="cuda")
     del x
-    plan = sc5.Plan(Pc, Hc, Wc, pitch, opitch, dt, odt, "valid", c["algo"], th, tw, st, c["ctas"], layout=c["layout"])
+    plan = sc5.Plan(Pc, Hc, Wc, pitch, opitch, dt, odt, "valid", c["algo"], th, tw, st, c["ctas"], layout=c["layout"],
+                    taps=n)
     k = synth.kernel_normalised(SEED)
+    if n != 5:
+        kn = synth.rng(100 + n).uniform(0, 1, n)
+        k = (kn / kn.sum()).astype(np.float32)
     out_scale = scale if odt == "fp8e4m3" else 1.0
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 0)):
