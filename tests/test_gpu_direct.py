@@ -131,3 +131,27 @@ def test_keep_border_and_refusals(sc5):
     with pytest.raises(sc5.Sepconv5Error):
         plan.run_K(U.to_dev(A), out, K)
     plan.close()
+
+
+def test_direct_8192_every_pixel(sc5):
+    """The direct single pass (25 products per output) on the 3 x 8192 x 8192
+    FP32 image in the launch configuration the benchmark times (the
+    planner's default direct plan): every output pixel against the FP64
+    oracle in bands of 512 output rows."""
+    import torch
+    P, H, W = 3, 8192, 8192
+    A = synth.image(2, H, W)
+    k = synth.kernel_normalised(2)
+    out = torch.empty((P, H - 4, W - 4), dtype=torch.float32, device="cuda")
+    plan = sc5.Plan(P, H, W, W, W - 4, algo="direct")
+    plan.run(U.to_dev(A), out, k)
+    torch.cuda.synchronize()
+    plan.close()
+    assert sc5.device_status() == 0
+    got = out.cpu().numpy()
+    del out
+    k64 = k.astype(np.float64)
+    for r0 in range(0, H - 4, 512):
+        r1 = min(H - 4, r0 + 512)
+        ref = oracle.direct(A[:, r0:r1 + 4, :].astype(np.float64), k64)
+        assert U.max_abs(got[:, r0:r1, :], ref) <= U.FP32_TOL, r0

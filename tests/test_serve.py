@@ -21,6 +21,8 @@ from tests import _util as U
 pytestmark = pytest.mark.gpu
 
 SIZES = [(5, 5), (64, 64), (131, 301), (480, 640), (1080, 1920), (67, 1030)]
+# fill of the output rows' padding, which the server must leave as it was
+PAD_FILL = {"f32": float("nan"), "bf16": -1, "f16": -1, "fp8e4m3": 0xFF}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +44,7 @@ def _request(i, H, W, dtype):
     tdt = {"bf16": torch.int16, "f16": torch.int16, "fp8e4m3": torch.uint8, "f32": torch.float32}[dtype]
     src = torch.from_numpy(padded.view(np.int16) if padded.dtype == np.uint16 else padded).pin_memory()
     op = U.pitch_for(W - 4, dtype)
-    dst = torch.full((3, H - 4, op), -1 if dtype != "f32" else float("nan"), dtype=tdt).pin_memory()
+    dst = torch.full((3, H - 4, op), PAD_FILL[dtype], dtype=tdt).pin_memory()
     k = synth.kernel_normalised(5000 + i)
     return {"in": src, "out": dst, "H": H, "W": W, "in_pitch": pitch, "out_pitch": op, "k": k,
             "in_scale": scale, "out_scale": scale}, padded
@@ -59,7 +61,7 @@ def _solo(sc5, req, dtype):
     return out.cpu()
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+@pytest.mark.parametrize("dtype", ["bf16", "f32", "f16", "fp8e4m3"])
 def test_same_alone_and_in_the_mix(sc5, dtype):
     import torch
     reqs = [_request(i, H, W, dtype) for i, (H, W) in enumerate(SIZES * 4)]
@@ -92,13 +94,14 @@ def test_same_alone_and_in_the_mix(sc5, dtype):
         W = req["W"]
         assert torch.equal(solo[:, :, :W - 4], req["out"][:, :, :W - 4]), (req["H"], W)
         pad = req["out"][:, :, W - 4:]
-        assert (torch.isnan(pad).all() if dtype == "f32" else (pad == -1).all()), "row padding written"
-        got = U.decode(U.from_dev(req["out"], dtype)[:, :, :W - 4], dtype)
-        ref = U.oracle_valid(padded, dtype, req["k"], W=W)
+        assert (torch.isnan(pad).all() if dtype == "f32" else (pad == PAD_FILL[dtype]).all()), "row padding written"
+        # real units: codes divided by the per-image scale (1 except for fp8)
+        got = U.decode(U.from_dev(req["out"], dtype)[:, :, :W - 4], dtype, req["out_scale"])
+        ref = U.oracle_valid(padded, dtype, req["k"], req["in_scale"], W=W)
         if dtype == "f32":
             assert U.max_abs(got, ref) <= U.FP32_TOL
         else:
-            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, 1.0, U.FP32_TOL))
+            assert np.all(np.abs(got - ref) <= U.stored_tolerance(ref, dtype, req["out_scale"], U.FP32_TOL))
 
 
 # The request sizes of the serving stream (640x480, 1920x1080, 4096x4096), two
