@@ -197,3 +197,18 @@ def test_device_waits_are_bounded_and_nothing_traps():
     body = dev[dev.index("bool mbar_wait_bounded("):]
     body = body[:body.index("\n}\n")]
     assert "global_timer_ns()" in body and "return false" in body
+
+
+def test_bench_case_parsing():
+    """`bench.py --case` options: defaults (3 x 8192 x 8192 FP32 fused, width 5),
+    integer keys parsed as integers, the output format defaulting to the
+    input's, and unknown keys refused."""
+    import bench
+    c = bench.parse_case("")
+    assert (c["dtype"], c["out"], c["algo"], c["H"], c["W"], c["taps"], c["batch"]) == \
+        ("f32", "f32", "fused", 8192, 8192, 5, 0)
+    c = bench.parse_case("dtype=bf16,tile=128x256x2,ctas=2,batch=256,taps=3,opitch=8196")
+    assert c["out"] == "bf16" and c["tile"] == "128x256x2"
+    assert (c["ctas"], c["batch"], c["taps"], c["opitch"]) == (2, 256, 3, 8196)
+    with pytest.raises(SystemExit):
+        bench.parse_case("colour=red")
