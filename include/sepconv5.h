@@ -373,6 +373,15 @@ SC5_API sc5_status sepconv5_fused_configs(int32_t in_dtype, int32_t out_dtype, i
  * for its test images. */
 SC5_API sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int32_t n_pairs,
                              const char *path);
+/* The same from the environment, without code changes, once per dtype pair on
+ * the pair's first plan, batch or server in the process:
+ *   SEPCONV5_TUNE_FILE=path   load a table written by sepconv5_autotune, and
+ *                             write the table back there after tuning;
+ *   SEPCONV5_TUNE=quick|full  tune the pair (modes 1 and 2 above) unless the
+ *                             table already holds all of its entries; that
+ *                             call then takes a few seconds;
+ *   SEPCONV5_TUNE=off or unset: built-in defaults unless a table is loaded.
+ * Failures leave the defaults in place. */
 /* Load a table written by sepconv5_autotune (entries for other GPUs are ignored). */
 SC5_API sc5_status sepconv5_tune_load(const char *path);
 /* The shape a plan would pick for a plane of H x W with these dtypes:

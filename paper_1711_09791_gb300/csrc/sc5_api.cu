@@ -283,6 +283,7 @@ sc5_status choose_shape(int in_dtype, int out_dtype, int H, int W, const sc5_pla
         *ctas = (ov && ov->ctas_per_sm > 0) ? ov->ctas_per_sm : fused_default_ctas(in_dtype, out_dtype, 0, direct, taps);
     } else {
         int th, tw, stg, c;
+        tune_from_environment(in_dtype, out_dtype);
         // the table's entry, else the shape's own default (0: as many as fit);
         // the descriptor overrides either
         *ctas = 0;
@@ -999,6 +1000,7 @@ sc5_status build_batch(const sc5_plan_desc &pd, int n, const sc5_image *imgs, co
 sc5_status choose_batch_shape(int in_dtype, int out_dtype, int n, const sc5_image *imgs, int *idx, int *ctas)
 {
     if (n < 1 || !imgs) return fail(SC5_EINVAL, "empty batch");
+    tune_from_environment(in_dtype, out_dtype);
     double by_class[64] = {};
     for (int i = 0; i < n; ++i) {
         const double px = static_cast<double>(imgs[i].H) * imgs[i].W;

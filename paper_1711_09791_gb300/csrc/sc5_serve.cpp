@@ -39,6 +39,7 @@
 
 #include "sc5_internal.h"
 #include "sc5_serve_host.h"
+#include "sc5_tune.h"
 
 namespace sc5 {
 
@@ -427,6 +428,7 @@ extern "C" sc5_status serve_create(const sc5_serve_cfg *cfg, sc5_server *out)
     e = cudaMemsetAsync(s->arena_base, 0, cfg->hbm_budget_bytes, s->s_h2d);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->desc_dev, 0, kDescBytes, s->s_h2d);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_h2d);
+    tune_from_environment(cfg->dtype, cfg->dtype);  // here rather than on the scheduler thread
     for (int i = 0; i < fused_num_shapes(cfg->dtype, cfg->dtype) && e == cudaSuccess; ++i)
         e = fused_prepare(cfg->dtype, cfg->dtype, i);
     for (int i = 0; i < 2 * cfg->max_inflight && e == cudaSuccess; ++i) {

@@ -12,8 +12,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sc5_internal.h"
@@ -257,6 +260,36 @@ extern "C" sc5_status sepconv5_autotune(int32_t mode, const int32_t *dtypes, int
         }
     }
     return path ? save_table(path) : SC5_OK;
+}
+
+void sc5::tune_from_environment(int in_dtype, int out_dtype)
+{
+    const char *mode = std::getenv("SEPCONV5_TUNE");
+    const char *file = std::getenv("SEPCONV5_TUNE_FILE");
+    if (!mode && !file) return;
+    static std::mutex mu;
+    static bool file_loaded = false;
+    static std::set<std::pair<int, int>> seen;
+    {
+        // Marked before tuning, so that the plans the tuner itself creates
+        // (and plans made meanwhile on other threads) keep the defaults.
+        std::lock_guard<std::mutex> lk(mu);
+        if (!seen.insert({in_dtype, out_dtype}).second) return;
+        if (file && !file_loaded) {
+            file_loaded = true;
+            sepconv5_tune_load(file);
+        }
+    }
+    const int m = !mode ? 0 : std::strcmp(mode, "quick") == 0 ? 1 : std::strcmp(mode, "full") == 0 ? 2 : 0;
+    if (m == 0) return;
+    int have = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (const auto &e : g_table) have += (e.in == in_dtype && e.out == out_dtype);
+    }
+    if (have >= 2 * kNumClasses) return;
+    const int32_t pair[2] = {in_dtype, out_dtype};
+    sepconv5_autotune(m, pair, 1, file);
 }
 
 extern "C" sc5_status sepconv5_tune_load(const char *path)

@@ -22,4 +22,16 @@ constexpr int kKindSingle = 0, kKindBatch = 1;
 bool tune_lookup_internal(int in_dtype, int out_dtype, int H, int W, int kind, int *tile_h, int *tile_w,
                           int *stages, int *ctas_per_sm);
 
+// The environment override, applied once per dtype pair on the pair's first
+// plan, batch or merged serving launch in the process:
+//   SEPCONV5_TUNE_FILE=path   load a saved table (entries for other GPUs are
+//                             ignored) and write the table back there after
+//                             tuning;
+//   SEPCONV5_TUNE=off         the built-in defaults unless a table is loaded;
+//   SEPCONV5_TUNE=quick|full  tune the pair (3 or 10 repetitions per
+//                             configuration, a few seconds of GPU time) unless
+//                             the table already holds all of its entries.
+// Failures leave the defaults in place (and a message in sepconv5_last_error).
+void tune_from_environment(int in_dtype, int out_dtype);
+
 }  // namespace sc5

@@ -52,3 +52,46 @@ def test_autotune_table_roundtrip(tmp_path):
     b.close()
     plan.close()
     sc5.autotune(0, [])
+
+
+def _child(code, env_extra):
+    import os
+    import subprocess
+    import sys
+    import textwrap
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if not k.startswith("SEPCONV5_TUNE")}
+    env.update(env_extra, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", textwrap.dedent(code)], env=env, capture_output=True, text=True,
+                       timeout=600, cwd=root)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return r.stdout.strip().splitlines()[-1]
+
+
+def test_tuning_from_the_environment(tmp_path):
+    """SEPCONV5_TUNE=quick with SEPCONV5_TUNE_FILE: the first plan of a dtype
+    pair tunes that pair and writes the table; a later process with only
+    SEPCONV5_TUNE_FILE loads it, and its plans take the tuned entries."""
+    path = str(tmp_path / "env_tune.json")
+    code = """
+        import json
+        from paper_1711_09791_gb300 import sepconv5 as sc5
+        sc5.load()
+        p = sc5.Plan(3, 4096, 4096, 4096, 4092, "bf16")
+        info = p.info()
+        p.close()
+        cfg, found = sc5.tune_lookup("bf16", "bf16", 4096, 4096)
+        print(json.dumps({"info": info, "cfg": cfg, "found": found}))
+    """
+    first = json.loads(_child(code, {"SEPCONV5_TUNE": "quick", "SEPCONV5_TUNE_FILE": path}))
+    table = json.load(open(path))
+    pairs = {(e["in"], e["out"]) for e in table["entries"]}
+    assert pairs == {(1, 1)} and len(table["entries"]) == 2 * 7
+    assert first["found"]
+    second = json.loads(_child(code, {"SEPCONV5_TUNE_FILE": path}))
+    assert second["found"] and second["cfg"] == first["cfg"]
+    for key in ("tile_h", "tile_w", "stages", "ctas_per_sm"):
+        assert second["info"][key] == second["cfg"][key], key
+    # without the variables a process keeps the built-in defaults
+    third = json.loads(_child(code, {}))
+    assert not third["found"]
