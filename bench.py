@@ -230,7 +230,8 @@ class ClockSampler:
         # median over the warm-up and timed steps (and the first sample after them)
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm), "samples_in_window": len(inside), "period_ms": self.PERIOD_MS,
-                "window": "warm-up and timed steps of the headline, plus the next sample"}
+                "window": "warm-up and timed steps of the headline and 0.25 s of the same launches right "
+                          "after them (untimed), plus the next sample"}
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -828,10 +829,17 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sampler = ClockSampler(smi_index)
     sampler.start()
     sampler.mark(0)
-    if rows:
-        ms, launches = timed(lambda: band.run(band_in, band_out, k, stream=stream), args.steps, max(args.warmup, 3))
-    else:
-        ms, launches = timed(lambda: plan.run(A_dev, out, k, stream=stream), args.steps, max(args.warmup, 3))
+    step = (lambda: band.run(band_in, band_out, k, stream=stream)) if rows else \
+        (lambda: plan.run(A_dev, out, k, stream=stream))
+    ms, launches = timed(step, args.steps, max(args.warmup, 3))
+    # A timed region of a few milliseconds falls between two clock samples:
+    # the same launches keep running, untimed and uncounted, for a quarter of
+    # a second after it so that the sampler sees the GPU under this load.
+    t_soak = time.perf_counter() + 0.25
+    while time.perf_counter() < t_soak:
+        for _ in range(16):
+            step()
+        torch.cuda.synchronize(dev)
     band.close()
     sampler.mark(1)
     clocks = sampler.stop()
