@@ -43,7 +43,7 @@ def _worker(rank, world, port, results):
 
 def test_two_gloo_ranks():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a threaded process
         results = mgr.dict()
         mp.spawn(_worker, args=(2, port, results), nprocs=2, join=True)
         r = dict(results)
