@@ -529,7 +529,7 @@ def leg_batch(sc5, synth, stream, dtypes):
             "bound": bound,
             "ms": round(ms, 4), "mpix_s": round(px / (ms / 1e3) / 1e6, 1), "achieved_gbs": round(alg / ms / 1e6, 1),
             "frac_of_measured_hbm": round(alg / ms / 1e6 / peak, 4),
-            "fma_tflops": round(outputs * FMA_PER_OUTPUT / (ms / 1e3) / 1e12, 2),
+            "tera_fma_per_s": round(outputs * FMA_PER_OUTPUT / (ms / 1e3) / 1e12, 2),
             "frac_of_fma_peak": round(outputs * FMA_PER_OUTPUT / (ms / 1e3) / fma_peak(), 4),
             "tiles": info["tiles"], "ctas": info["ctas"],
             "tile": f"{info['tile_h']}x{info['tile_w']}", "create_ms": round(create_ms, 1)}
