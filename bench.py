@@ -321,42 +321,47 @@ def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
             "both_2streams_gbs": round((nb_in + nb_out) / ts / 1e6, 1)}
 
 
-def link_stalls(seconds: float = 3.0, nbytes: int = 3 * 1076 * 1916 * 2) -> dict:
-    """Plain back-to-back copies of a 1920x1080 BF16 output in both directions
-    at once (no server involved) for a few seconds; the gaps between
-    consecutive copy completions on the device clock show how often, and for
-    how long, the CPU-GPU link stalls."""
+def device_pauses(seconds: float = 6.0, ahead: int = 2000) -> dict:
+    """Back-to-back device work with `ahead` launches (about 80 ms of work)
+    queued in front of the host, so that no host hiccup can empty the queue:
+    an elementwise kernel over 120 MB on one stream and a 12 MB
+    device-to-device copy on another, for a few seconds.  A gap of more than
+    5 ms between consecutive completions on one stream is the GPU itself
+    pausing; the lists give when (seconds from the start) and for how long."""
     import torch
-    hbuf = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(4)]
-    dbuf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    dsrc = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    s_d, s_h = torch.cuda.Stream(), torch.cuda.Stream()
+    x = torch.rand(30 << 20, device="cuda")
+    y = torch.empty_like(x)
+    src = torch.empty(12 << 20, dtype=torch.uint8, device="cuda")
+    dst = torch.empty_like(src)
+    sk, sc = torch.cuda.Stream(), torch.cuda.Stream()
     base = torch.cuda.Event(enable_timing=True)
-    base.record(s_d)
+    base.record(sk)
     base.synchronize()
-    evs = {"d2h": [], "h2d": []}
-    t0, i = time.perf_counter(), 0
+    evs = {"kernel": [], "d2d_copy": []}
+    t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds:
-        for _ in range(16):
-            with torch.cuda.stream(s_d):
-                hbuf[i % 4].copy_(dsrc, non_blocking=True)
+        for _ in range(8):
+            with torch.cuda.stream(sk):
+                torch.mul(x, 1.0001, out=y)
                 e = torch.cuda.Event(enable_timing=True)
-                e.record(s_d)
-                evs["d2h"].append(e)
-            with torch.cuda.stream(s_h):
-                dbuf.copy_(hbuf[(i + 2) % 4], non_blocking=True)
+                e.record(sk)
+                evs["kernel"].append(e)
+            with torch.cuda.stream(sc):
+                dst.copy_(src, non_blocking=True)
                 e = torch.cuda.Event(enable_timing=True)
-                e.record(s_h)
-                evs["h2d"].append(e)
-            i += 1
-        evs["h2d"][-1].synchronize()
+                e.record(sc)
+                evs["d2d_copy"].append(e)
+        if len(evs["kernel"]) > ahead:
+            evs["kernel"][-ahead].synchronize()
     torch.cuda.synchronize()
-    out = {"seconds": seconds, "copies_per_direction": i, "bytes_each": nbytes}
+    out = {"seconds": seconds, "queued_ahead": ahead, "launches_per_stream": len(evs["kernel"])}
     for kind, lst in evs.items():
         ts = [base.elapsed_time(e) for e in lst]
-        gaps = sorted(b - a for a, b in zip(ts, ts[1:]))
-        out[kind] = {"median_gap_ms": round(gaps[len(gaps) // 2], 4), "max_gap_ms": round(gaps[-1], 3),
-                     "gaps_over_5ms": sum(g > 5.0 for g in gaps)}
+        gaps = [b - a for a, b in zip(ts, ts[1:])]
+        srt = sorted(gaps)
+        out[kind] = {"median_gap_ms": round(srt[len(srt) // 2], 4), "max_gap_ms": round(srt[-1], 3),
+                     "pauses_over_5ms": [[round(t / 1e3, 2), round(g, 1)] for t, g in zip(ts[1:], gaps) if g > 5.0][:12]}
+    del x, y, src, dst
     return out
 
 
@@ -638,7 +643,7 @@ def leg_serve(sc5, synth, n_req, link=None):
         sat["link_ceiling_req_s"] = round(both * 1e9 / bytes_per_req, 1)
         sat["frac_of_link"] = round(rate_sat * bytes_per_req / (both * 1e9), 4)
     out["saturation_bf16_merged"] = sat
-    out["link_stalls"] = link_stalls(6.0)
+    out["device_pauses"] = device_pauses(6.0)
     pool_f32 = make_pool("f32", 8)
     for frac in (0.5, 0.8, 0.95):
         rate = frac * rate_sat
