@@ -271,18 +271,23 @@ def cpu_two_pass_sample(A: np.ndarray, k: np.ndarray) -> dict:
 
 def copy_probe(A_host, out_host, A_dev, out_dev, dev) -> dict:
     """Copy-only times for the offload bytes: host->device alone,
-    device->host alone, and both at once on two streams."""
+    device->host alone, and both at once on two streams (each the median of
+    7 repetitions)."""
     import torch
     s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def t(fn, reps=5):
+    def t(fn, reps=7):
+        # median of separately timed repetitions: one that meets a pause of
+        # the GPU (tens of milliseconds, about every 2 s) does not move it
         fn()
         torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
+        ts = []
         for _ in range(reps):
+            t0 = time.perf_counter()
             fn()
-        torch.cuda.synchronize(dev)
-        return (time.perf_counter() - t0) * 1e3 / reps
+            torch.cuda.synchronize(dev)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return sorted(ts)[reps // 2]
 
     def h2d():
         with torch.cuda.stream(s1):
