@@ -636,7 +636,9 @@ def leg_serve(sc5, synth, n_req, link=None):
         return res
 
     pool_bf = make_pool("bf16", 8)
-    sat = run("bf16", True, 0.0, min(n_req, 2000), pool_bf, 11)
+    # saturation: a burst long enough (about 2 s) to include a pause of the
+    # GPU, so that the offered loads below are fractions of a sustained rate
+    sat = run("bf16", True, 0.0, min(n_req, 8000), pool_bf, 11)
     rate_sat = sat["achieved_req_s"]
     # the link ceiling of this mix: each request's input crosses host->device
     # and its output device->host, both directions at once
