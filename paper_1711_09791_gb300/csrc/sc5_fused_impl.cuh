@@ -14,11 +14,14 @@
 //     refills a stage only after every consumer warp has released it on
 //     `empty[s]`.
 //   * warps 0..NC-1 (consumers) -- warp w owns output rows [w*R, w*R+R) of the
-//     tile, lane l owns output columns [4l, 4l+4).  For each of its R+4 input
-//     rows a lane reads 8 stored values from shared memory, widens them to
-//     FP32, forms the 4 horizontal-pass values, and adds each into the (at
-//     most 5) pending output rows it contributes to; an output row is stored
-//     as soon as its fifth tap has arrived.  Stores are 4-wide and streaming.
+//     tile, lane l owns output columns [4l, 4l+4).  (A batch tile of 8/16-bit
+//     input at most 64 columns wide: half-warp h of warp w < NC/2 owns the
+//     rows of strip w + h*NC/2, lane l columns [4(l%16), 4(l%16)+4).)  For
+//     each of its R+4 input rows a lane reads 8 stored values from shared
+//     memory, widens them to FP32, forms the 4 horizontal-pass values, and
+//     adds each into the (at most 5) pending output rows it contributes to;
+//     an output row is stored as soon as its fifth tap has arrived.  Stores
+//     are 4-wide and streaming.
 // All waits are bounded by global time; on time-out the kernel records an
 // error in the status word and returns (no trap).
 #pragma once
@@ -443,11 +446,20 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
             load_staged(sdesc[s]);
         else if constexpr (BATCH)
             load_desc(descs[rec.img]);
-        const int ry0 = rec.ty * TH + warp * R;
-        const int cx = rec.tx * TW + lane * COLS;
+        // A batch tile at most half a tile wide (an image's last tile column)
+        // is covered by half the warps, each half-warp taking one row strip:
+        // the 8/16-bit kernels are bound by issue and the FMA pipe, and the
+        // other half of each warp would idle past the image's right edge.
+        constexpr bool kHalfEdge =
+            BATCH && !DIRECT && sizeof(TIn) < 4 && COLS == kColsPerThread && NBOX == 1 && NC % 2 == 0;
+        const bool halfw = kHalfEdge && Wv - rec.tx * TW <= TW / 2;
+        const int strip = halfw ? warp + (lane >> 4) * (NC / 2) : warp;  // row strip of the tile
+        const int cl = halfw ? (lane & 15) : lane;                        // column group of the strip
+        const int ry0 = rec.ty * TH + strip * R;
+        const int cx = rec.tx * TW + cl * COLS;
         const int rows_valid = min(R, Hv - ry0);
         const int cols_valid = min(COLS, Wv - cx);
-        const bool active = rows_valid > 0 && cols_valid > 0;
+        const bool active = (!halfw || warp < NC / 2) && rows_valid > 0 && cols_valid > 0;
         // The warp runs the guard-free strip only if every active lane's strip
         // is interior: a warp with one edge lane then runs the guarded strip
         // alone instead of both (both give the same values).
@@ -456,8 +468,8 @@ fused_kernel(const __grid_constant__ ImgDesc single, const ImgDesc *__restrict__
         if (active) {
             // lanes 0-15 of a 256-wide tile read the first box, lanes 16-31 the second
             const int box = NBOX == 2 ? (lane >> 4) : 0;
-            const int bl = NBOX == 2 ? (lane & 15) : lane;
-            const TIn *src = reinterpret_cast<const TIn *>(smem + s * STAGE + box * BOXB) + (warp * R) * BW +
+            const int bl = NBOX == 2 ? (lane & 15) : cl;
+            const TIn *src = reinterpret_cast<const TIn *>(smem + s * STAGE + box * BOXB) + (strip * R) * BW +
                              bl * COLS;
             TOut *dst = reinterpret_cast<TOut *>(out_base) + rec.plane * out_plane +
                         static_cast<int64_t>(ry0) * out_pitch + cx;
